@@ -1,0 +1,90 @@
+"""The oracle's pins must catch plausible mistakes.
+
+Each case plants one mistake in a private copy of ``oracle/pano_oracle.c``
+(a flipped sign, a swapped operand, a dropped term ...), compiles it on the
+CPU, points the oracle front end at the mutant and runs the pins of
+``test_oracle_pins``. At least one pin must fail for every mutant. The real
+oracle is restored afterwards.
+"""
+import os
+import subprocess
+
+import pytest
+
+import oracle
+from tests import test_oracle_pins as pins
+
+SRC = os.path.join(os.path.dirname(oracle.__file__), "pano_oracle.c")
+
+# (name, original text, planted mistake)
+MUTANTS = [
+    ("It sign", "- T[q];\n            s[q]", "+ T[q];\n            s[q]"),
+    ("s uses Iy for x", "s[q] = Ix[q] * u[2 * q] + Iy[q]", "s[q] = Iy[q] * u[2 * q] + Iy[q]"),
+    ("s drops linearisation", "s[q] = Ix[q] * u[2 * q] + Iy[q] * u[2 * q + 1] - It;", "s[q] = -It;"),
+    ("damping term dropped", "double r1 = m1 + lambda * u[2 * p]", "double r1 = m1 + 0.0 * u[2 * p]"),
+    ("solve transposed", "v[2 * p + 0] = (a22 * r1 - g12 * r2) / det;", "v[2 * p + 0] = (a11 * r1 - g12 * r2) / det;"),
+    ("window clamped not clipped", "if (qx < 0 || qx >= w) continue;", "if (0) continue;"),
+    ("upsample not doubled", "uf[2 * p + 0] = 2.0 *", "uf[2 * p + 0] = 1.0 *"),
+    ("upsample wrong scale", "0.5 * x, 0.5 * y);\n            uf[2 * p + 1]", "0.5 * x, 0.5 * x);\n            uf[2 * p + 1]"),
+    ("pyramid odd kernel", "{1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16}", "{1.0 / 16, 4.0 / 16, 6.0 / 16, 5.0 / 16, 0.0 / 16}"),
+    ("pyramid keeps odd rows", "int y = 2 * yd, x = 2 * xd;", "int y = 2 * yd + 1, x = 2 * xd;"),
+    ("bilinear fx/fy swapped", "(1.0 - fy) * ((1.0 - fx) * i00 + fx * i10)", "(1.0 - fx) * ((1.0 - fy) * i00 + fy * i10)"),
+    ("gradient halved twice", "PIX(Ix, w, y, x) = 0.5 *", "PIX(Ix, w, y, x) = 0.25 *"),
+    ("luma weights", "0.299 * img[3 * i + 0] + 0.587", "0.587 * img[3 * i + 0] + 0.299"),
+    ("blend position uses BlendL", "double Lx = x + rlx * (1.0 - blendL)", "double Lx = x + rlx * blendL"),
+    ("blend flow roles swapped", "double Rx = x + lrx * (1.0 - blendR)", "double Rx = x + rlx * (1.0 - blendR)"),
+    ("FlowMag roles swapped", "double expL = exp(k_sharp * blendL * (1.0 + k_mag * magRL));",
+     "double expL = exp(k_sharp * blendL * (1.0 + k_mag * magLR));"),
+    ("softmax sign", "double expR = exp(k_sharp * blendR", "double expR = exp(-k_sharp * blendR"),
+    ("Eq1 ramp off by one", "out[x] = (double)(x + 1) / (double)(w + 1);", "out[x] = (double)(x) / (double)(w + 1);"),
+    ("Eq1 distance squared", "double d = sqrt(", "double d = ("),
+    ("quantize truncates", "double v = nearbyint(255.0 * F[i]);", "double v = floor(255.0 * F[i]);"),
+]
+
+PIN_TESTS = [
+    lambda: pins.test_luma_gray_is_identity_and_weights_are_bt601(),
+    lambda: [pins.test_pyr_down_matches_scipy_binomial_reduce(s) for s in [(7, 9), (8, 8)]],
+    lambda: pins.test_bilinear_matches_scipy_order1_nearest(),
+    lambda: pins.test_gradient_is_central_difference_with_replicate_border(),
+    lambda: [pins.test_lk_step_matches_bruteforce_least_squares(r, l) for r, l in [(1, 1e-3), (2, 1e-2)]],
+    lambda: pins.test_lk_step_integer_translation_is_a_fixed_point_and_attracts(),
+    lambda: pins.test_upsample_flow_matches_scipy_and_doubles(),
+    lambda: pins.test_flow_pair_recovers_subpixel_translation(),
+    lambda: pins.test_flow_pair_needs_the_pyramid_for_large_motion(),
+    lambda: [pins.test_blend_coeff_golden_eq1(c) for c in pins._read_golden_canvases()],
+    lambda: [pins.test_blend_ramp_is_eq1_for_a_strip(w) for w in (4, 9)],
+    lambda: [pins.test_blend_closed_form_for_constant_translation(d) for d in [(2.0, -1.0)]],
+    lambda: pins.test_blend_swap_symmetry_exact(),
+    lambda: pins.test_blend_mirror_symmetry_with_strip_ramp(),
+    lambda: pins.test_blend_weights_sum_to_one_and_follow_the_blend_coefficient(),
+    lambda: pins.test_blend_larger_RtoL_flow_pulls_weight_towards_L(),
+    lambda: pins.test_quantize_u8_rounds_half_to_even_and_clamps(),
+]
+
+
+def _build_mutant(tmp_path, name, old, new):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation anchor for {name!r} not unique in the oracle source"
+    mpath = tmp_path / "mutant.c"
+    mpath.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O1", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                           "-ffp-contract=off", str(mpath), "-o", str(so), "-lm"])
+    return str(so)
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(tmp_path, monkeypatch, name, old, new):
+    so = _build_mutant(tmp_path, name, old, new)
+    monkeypatch.setattr(oracle, "_lib", None)
+    monkeypatch.setattr(oracle, "build", lambda force=False: so)
+    caught = []
+    try:
+        for i, t in enumerate(PIN_TESTS):
+            try:
+                t()
+            except AssertionError:
+                caught.append(i)
+    finally:
+        oracle._lib = None
+    assert caught, f"no pin caught the planted mistake {name!r}"
