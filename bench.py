@@ -1,0 +1,386 @@
+#!/usr/bin/env python
+"""Throughput of the asymmetric bidirectional optical-flow blend on GB300.
+
+One step = the whole path for one overlap pair: luma + Gaussian pyramids of
+both strips, pyramidal LK flow in both directions, and the Code 1 blend
+(pano_flow_pair + pano_blend_pair). Workload: a 4000x1500 RGB uint8 pair,
+6 pyramid levels, 5 LK steps per level, 5x5 window (synthetic, seeded).
+The metric is overlap megapixels per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+With N > 1 (under torchrun) every rank runs its own pair: the pairs are
+independent, there is no data exchange, and the reported value is the pixels
+of all ranks over the slowest rank's time. ``--impl reference`` times the
+FP64 CPU oracle instead (on rank 0 only), on row bands of the same pair.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "overlap megapixels/sec (bi-flow+warp+blend) on 1 GB300; % HBM roofline; EPE vs oracle"
+UNIT = "MP/s"
+WORKLOAD = {"workload": "pair_4000x1500_rgb_u8_lv6", "h": 4000, "w": 1500, "channels": 3, "levels": 6,
+            "iters": 5, "radius": 2}
+L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+
+
+# ---------------------------------------------------------------------------
+# host-side helpers (no GPU needed; covered by the CPU tests)
+# ---------------------------------------------------------------------------
+
+def level_pixels(h: int, w: int, levels: int):
+    out = []
+    for _ in range(levels):
+        out.append(h * w)
+        h, w = (h + 1) // 2, (w + 1) // 2
+    return out
+
+
+def lk_alg_bytes(h: int, w: int, levels: int):
+    """Algorithmic bytes of each LK level launch (both directions).
+
+    Per direction and level pixel: read the template and target levels
+    (4 + 4 B), read the coarse flow (8 B per coarse pixel = 2 B per fine
+    pixel; none at the coarsest level), write the flow (8 B).
+    """
+    npx = level_pixels(h, w, levels)
+    out = []
+    for l, n in enumerate(npx):
+        coarse = 8 * npx[l + 1] if l + 1 < levels else 0
+        out.append(2 * (8 * n + coarse + 8 * n))
+    return out
+
+
+def path_alg_bytes(h: int, w: int, c: int, levels: int, in_bytes: int = 1):
+    """Algorithmic bytes of one step of the whole path (each array once)."""
+    npx = level_pixels(h, w, levels)
+    n = h * w
+    pyramid = 2 * c * in_bytes * n + 2 * 4 * sum(npx) + 2 * 4 * sum(npx[:-1])  # read strips, write levels, re-read for REDUCE
+    flow = sum(lk_alg_bytes(h, w, levels))
+    blend = 2 * c * in_bytes * n + 16 * n + c * in_bytes * n
+    return pyramid + flow + blend
+
+
+def throughput(pixels_per_step: int, steps: int, world: int, max_total_ms: float) -> float:
+    """Whole-job MP/s: every rank's pixels over the slowest rank's time."""
+    return pixels_per_step * steps * world / (max_total_ms * 1e-3) / 1e6
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int) -> None:
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def read_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle timing (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+
+def time_oracle(pair, levels: int, budget_s: float, band_rows: int = 500, max_bands: int = 1000):
+    """Oracle stitch (flow + blend) on row bands of the pair until budget_s
+    of CPU work; returns (MP/s, threads, sample description, seconds)."""
+    import oracle
+    P = oracle.Params(levels=levels)
+    h = pair.L.shape[0]
+    done_px, t_total, bands = 0, 0.0, 0
+    y = 0
+    while (t_total < budget_s or bands == 0) and bands < max_bands:
+        y0 = y % max(1, h - band_rows + 1)
+        L = pair.L[y0:y0 + band_rows]
+        R = pair.R[y0:y0 + band_rows]
+        t0 = time.perf_counter()
+        oracle.stitch_pair(L, R, P)
+        t_total += time.perf_counter() - t0
+        done_px += L.shape[0] * L.shape[1]
+        bands += 1
+        y += band_rows
+    desc = f"{bands} bands of {band_rows}x{pair.L.shape[1]} rows of the pair (FP64 oracle, flow + blend)"
+    return done_px / t_total / 1e6, oracle.num_threads(), desc, t_total
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import synth
+    pair = synth.pair_fullres_rgb()
+    import oracle
+    oracle.build()
+    band = 250
+    vals = []
+    for i in range(args.warmup + args.steps):
+        v, cores, desc, _ = time_oracle(pair, WORKLOAD["levels"], 0.0, band_rows=band, max_bands=1)
+        if i >= args.warmup:
+            vals.append(v)
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": band * WORKLOAD["w"] / value / 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": dict(WORKLOAD, sample=f"one {band}-row band per step"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"one {band}x{WORKLOAD['w']} band of the pair per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import synth
+    import paper_2006_01201_gb300 as pkg
+    from paper_2006_01201_gb300 import build as gpu_build
+
+    gpu_build.build()
+    pkg.load_library()
+    h, w, c, levels = WORKLOAD["h"], WORKLOAD["w"], WORKLOAD["channels"], WORKLOAD["levels"]
+    pair = synth.pair_fullres_rgb(seed=1 + rank, h=h, w=w, levels=levels)
+    ctx = pkg.FlowContext(pkg.Params(levels=levels, iters=WORKLOAD["iters"], radius=WORKLOAD["radius"]),
+                          max_h=h, max_w=w, max_c=c)
+    L = torch.from_numpy(pair.L).to(dev)
+    R = torch.from_numpy(pair.R).to(dev)
+    lr = torch.empty((h, w, 2), dtype=torch.float32, device=dev)
+    rl = torch.empty((h, w, 2), dtype=torch.float32, device=dev)
+    F = torch.empty_like(L)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        ctx.flow_pair(L, R, out=(lr, rl), stream=stream)
+        ctx.blend_pair(L, R, lr, rl, out=F, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    # --- timed region: K steps, device-resident inputs, L2 flushed between steps
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = ctx.launches
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    launches = ctx.launches - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = reduce_max(sum(step_ms), world)
+    value = throughput(h * w, args.steps, world, total_ms)
+
+    # --- same loop with every launch bracketed by events: per-kernel times
+    ctx.trace_enable(0xF, 64 * args.steps)
+    for k in range(args.steps):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    recs = ctx.trace_read(64 * args.steps)
+    ctx.trace_enable(0, 0)
+    names = {1: "luma_kernel", 2: "pyr_down_kernel", 4: "lk_level_kernel", 8: "blend_kernel"}
+    per_kind = {}
+    for kind, lev, ms in recs:
+        d = per_kind.setdefault(names[kind], {"launches": 0, "ms": 0.0})
+        d["launches"] += 1
+        d["ms"] += ms
+    traced_total = sum(d["ms"] for d in per_kind.values())
+    for d in per_kind.values():
+        d["share"] = d["ms"] / traced_total if traced_total else None
+        d["ms_per_step"] = d["ms"] / args.steps
+    dominant = max(per_kind, key=lambda k: per_kind[k]["ms"])
+    lk_bytes_step = sum(lk_alg_bytes(h, w, levels))
+    lk_ms_step = per_kind["lk_level_kernel"]["ms"] / args.steps
+    peak, peak_src = read_peaks()
+    achieved = lk_bytes_step / (lk_ms_step * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": None, "kernel": "lk_level_kernel",
+                "alg_bytes_per_launch": lk_bytes_step / levels, "launch_ms": lk_ms_step / levels,
+                "peak_source": f"{peak_src} hbm_gbs"}
+    path_bytes = path_alg_bytes(h, w, c, levels)
+    path_gbs = path_bytes / (total_ms / args.steps * 1e-3) / 1e9
+
+    # --- end to end: pinned host strips in, F back to pinned host memory
+    Lh = torch.from_numpy(pair.L).pin_memory()
+    Rh = torch.from_numpy(pair.R).pin_memory()
+    Fh = torch.empty_like(Lh).pin_memory()
+    work = {"L": torch.empty_like(L), "R": torch.empty_like(R), "lr": torch.empty_like(lr),
+            "rl": torch.empty_like(rl), "F": torch.empty_like(F)}
+    for _ in range(max(1, args.warmup)):
+        ctx.stitch_host(Lh, Rh, Fh, work, stream=stream)
+    torch.cuda.synchronize()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        ctx.stitch_host(Lh, Rh, Fh, work, stream=stream)
+        ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev2), world)
+    e2e = {"value": throughput(h * w, args.steps, world, e2e_ms), "unit": UNIT,
+           "h2d_bytes_per_step": int(Lh.numel() + Rh.numel()), "d2h_bytes_per_step": int(Fh.numel()),
+           "ms_per_step": e2e_ms / args.steps}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(WORKLOAD, l2="flushed between steps (256 MB write, untimed)",
+                               parallelism=f"replicas{world}"),
+                "roofline": roofline,
+                "path": {"alg_bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / peak},
+                "kernels": per_kind, "dominant_kernel": dominant,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            # parity of this run's flows against the oracle, and the oracle's speed
+            t0 = time.perf_counter()
+            olr, orl = oracle.flow_pair(pair.L, pair.R, oracle.Params(levels=levels))
+            t_full = time.perf_counter() - t0
+            g_lr, g_rl = lr.cpu().numpy(), rl.cpu().numpy()
+            e_lr = float(np.hypot(*(g_lr - olr).transpose(2, 0, 1)).mean())
+            e_rl = float(np.hypot(*(g_rl - orl).transpose(2, 0, 1)).mean())
+            line["epe_vs_oracle"] = {"LtoR_mean_px": e_lr, "RtoL_mean_px": e_rl}
+            v, cores, desc, secs = time_oracle(pair, levels, budget_s=args.cpu_budget)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+                                    "seconds": secs, "full_pair_flow_s": t_full}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * pano_flow.h -- C ABI of the GB300 (sm_103a) asymmetric bidirectional
+ * optical-flow blend of two overlap strips.
+ *
+ * Method: Meng & Liu, "High-quality Panorama Stitching based on Asymmetric
+ * Bidirectional Optical Flow", Section III-C. Two already-aligned overlap
+ * strips OverlappedL / OverlappedR (Section III-C, the Area3 crop of images L
+ * and R) are blended into F through
+ *   - a Gaussian pyramid of each strip's luma,
+ *   - dense pyramidal Lucas-Kanade flow in both directions, FlowLtoR and
+ *     FlowRtoL (Section III-C-1),
+ *   - the global blending coefficient Blend, Eq. (1) (Section III-C-2),
+ *   - the flow warp and asymmetric softmax blend of Code 1 (Section III-C-3).
+ *
+ * Conventions shared by every call
+ *   Memory      All image and flow pointers are CUDA device memory owned by
+ *               the caller; the library never frees them. A context owns its
+ *               own scratch (pyramids and coarse-level flows), allocated once
+ *               by pano_flow_create and freed by pano_flow_destroy.
+ *   Streams     Every call only enqueues work on `cuda_stream` (a
+ *               cudaStream_t; NULL = the legacy default stream) and returns;
+ *               outputs are valid once that stream reaches them. No call
+ *               synchronises, allocates or frees device memory after
+ *               pano_flow_create, so a sequence of calls can be captured in a
+ *               CUDA graph. Use one context per stream; a context is not
+ *               thread-safe. Call with the context's device current.
+ *   Errors      Arguments are checked on the host before anything is
+ *               enqueued; a call that fails its checks enqueues nothing and
+ *               writes no output. CUDA errors map to PANO_ERR_CUDA. Nothing
+ *               throws or exits across this boundary. pano_last_error()
+ *               returns a message for the last failing call on the calling
+ *               thread.
+ *   Images      pano_image describes a row-major (h, w, c) image with
+ *               interleaved channels: sample (y, x, k) is at
+ *               data + y * pitch_bytes + (x * c + k) * element_size.
+ *               PANO_U8 samples are read as value / 255; PANO_F32 samples are
+ *               taken as they are (intended range [0, 1]).
+ *   Flows       A flow field is (h, w, 2) float32, contiguous (row pitch
+ *               w * 2 floats), 8-byte aligned: element [y][x][0] is the
+ *               column offset, [y][x][1] the row offset, in pixels.
+ *               FlowAtoB lives on A's grid and satisfies
+ *               A(p) ~ B(p + FlowAtoB(p)) (Section III-C-1: the flow of
+ *               OverlappedR relative to OverlappedL is FlowRtoL).
+ *   Borders     Every sampler clamps to the edge of the strip.
+ */
+#ifndef PANO_FLOW_H
+#define PANO_FLOW_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define PANO_API __attribute__((visibility("default")))
+#else
+#define PANO_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum pano_status {
+    PANO_OK = 0,
+    PANO_ERR_INVALID_ARG = 1,  /* null pointer, bad size, pitch or alignment */
+    PANO_ERR_UNSUPPORTED = 2,  /* valid request this build does not implement */
+    PANO_ERR_OOM = 3,          /* device allocation failed (create only) */
+    PANO_ERR_CUDA = 4,         /* a CUDA call or launch failed */
+    PANO_ERR_TIMEOUT = 5       /* reserved: a bounded device wait gave up */
+} pano_status;
+
+typedef enum pano_dtype {
+    PANO_U8 = 0,
+    PANO_F32 = 1,
+    PANO_BF16 = 2,   /* reserved */
+    PANO_F16 = 3     /* reserved */
+} pano_dtype;
+
+typedef struct pano_image {
+    void* data;          /* device pointer, aligned to the element size */
+    int h, w, c;         /* rows, columns, channels (1 or 3) */
+    size_t pitch_bytes;  /* bytes between rows, >= w * c * element size */
+    int dtype;           /* a pano_dtype */
+} pano_image;
+
+/* Method parameters. The paper publishes none of them (Section III-C-1
+ * leaves the Lucas-Kanade parameters open; Section III-C-3 names
+ * kSoftmaxSharpness and kFlowMagCoef without values). */
+typedef struct pano_flow_params {
+    int levels;           /* pyramid levels, 1..12 (default 4) */
+    int iters;            /* Lucas-Kanade steps per level, 0..16 (default 5) */
+    int radius;           /* window radius r, window (2r+1)^2, 1..3 (default 2) */
+    float lambda;         /* damping towards the current flow, >= 0 (default 1e-2) */
+    float soft_sharpness; /* kSoftmaxSharpness of Code 1 (default 10) */
+    float flow_mag_coef;  /* kFlowMagCoef of Code 1 (default 20) */
+    int pyr_dtype;        /* storage of pyramid levels; PANO_F32 only */
+} pano_flow_params;
+
+typedef struct pano_flow_ctx pano_flow_ctx;
+
+/* Fill *p with the defaults listed above. */
+PANO_API void pano_flow_params_default(pano_flow_params* p);
+
+/* Create a context for strips of at most max_h x max_w pixels and max_c
+ * channels on the current device, and allocate its scratch:
+ * two pyramids of float32 levels (~ 2 * 4 * (4/3) * max_h * max_w bytes) and
+ * the coarse-level flows of both directions (~ 2 * 8 * (1/3) * max_h * max_w
+ * bytes). *out receives the context; on failure *out is NULL.
+ * Errors: INVALID_ARG (null p/out, parameters out of range, sizes < 1),
+ * UNSUPPORTED (pyr_dtype other than PANO_F32), OOM, CUDA. */
+PANO_API pano_status pano_flow_create(const pano_flow_params* p, int max_h, int max_w, int max_c,
+                             pano_flow_ctx** out);
+
+/* Asymmetric bidirectional optical flow of a strip pair (Section III-C-1):
+ * FlowLtoR with L as template and R as target, FlowRtoL with the roles
+ * exchanged, each by pyramidal Lucas-Kanade over the luma of the strips
+ * (BT.601 for 3 channels). L and R must have the same h, w, c and dtype
+ * (PANO_U8 or PANO_F32, c = 1 or 3, within the context's maxima).
+ * flow_LtoR and flow_RtoL receive (h, w, 2) float32 fields as described
+ * under "Flows"; they must not overlap each other or the inputs.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+PANO_API pano_status pano_flow_pair(pano_flow_ctx* ctx, const pano_image* L, const pano_image* R,
+                           float* flow_LtoR, float* flow_RtoL, void* cuda_stream);
+
+/* Code 1 (Section III-C-3), Area3 branch, for every pixel p of the strips:
+ *   BlendL = 1 - Blend(p), BlendR = Blend(p)
+ *   ColorL = L(p + (1 - BlendL) FlowRtoL(p)),  ColorR = R(p + (1 - BlendR) FlowLtoR(p))
+ *   FlowL  = 1 + kFlowMagCoef |FlowRtoL(p)| / w,  FlowR = 1 + kFlowMagCoef |FlowLtoR(p)| / w
+ *   F(p)   = softmax-weighted sum of ColorL and ColorR with exponents
+ *            kSoftmaxSharpness * BlendL * FlowL and kSoftmaxSharpness * BlendR * FlowR,
+ * per channel, with bilinear clamp-to-edge sampling.
+ * blend: (h, w) float32 contiguous array of Blend values (Eq. 1), or NULL
+ * for the Eq. (1) value of a full-height strip with Area1 on its left and
+ * Area2 on its right, Blend(x) = (x + 1) / (w + 1).
+ * F: same h, w, c and dtype as L. PANO_U8 output is round-half-even of
+ * 255 * F clamped to [0, 255]; PANO_F32 output is F.
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA. */
+PANO_API pano_status pano_blend_pair(pano_flow_ctx* ctx, const pano_image* L, const pano_image* R,
+                            const float* flow_LtoR, const float* flow_RtoL, const float* blend,
+                            pano_image* F, void* cuda_stream);
+
+/* Free the context and its scratch. NULL is accepted. Work already enqueued
+ * that uses the context must have completed. */
+PANO_API pano_status pano_flow_destroy(pano_flow_ctx* ctx);
+
+/* Message describing the last failing call on the calling thread ("" if
+ * none). The pointer stays valid until the next call on this thread. */
+PANO_API const char* pano_last_error(const pano_flow_ctx* ctx);
+
+/* ----------------------------------------------------------------------
+ * Tracing. When enabled, every launch of a kernel kind selected by
+ * kind_mask that a context call enqueues is bracketed by two CUDA events on
+ * that call's stream, so its device time can be read back. Events are
+ * created by pano_trace_enable (not by the traced calls); at most `capacity`
+ * launches are recorded until the next pano_trace_read.
+ * ---------------------------------------------------------------------- */
+#define PANO_TRACE_LUMA     0x1u   /* level-0 luma */
+#define PANO_TRACE_PYR_DOWN 0x2u   /* pyramid REDUCE */
+#define PANO_TRACE_LK       0x4u   /* one Lucas-Kanade level, both directions */
+#define PANO_TRACE_BLEND    0x8u   /* Code 1 blend */
+
+typedef struct pano_trace_record {
+    int kind;     /* one PANO_TRACE_* bit */
+    int level;    /* pyramid level (LK, REDUCE destination), else 0 */
+    float ms;     /* device time between the two events */
+} pano_trace_record;
+
+/* Enable tracing of the kinds in kind_mask with room for `capacity`
+ * launches; capacity 0 (or kind_mask 0) disables it and frees the events.
+ * Errors: INVALID_ARG, OOM, CUDA. */
+PANO_API pano_status pano_trace_enable(pano_flow_ctx* ctx, unsigned kind_mask, int capacity);
+
+/* Wait for the recorded events, copy up to max_records records (launch
+ * order) to out, store their number in *n_out, and start a new recording.
+ * Errors: INVALID_ARG, CUDA. */
+PANO_API pano_status pano_trace_read(pano_flow_ctx* ctx, pano_trace_record* out, int max_records,
+                                     int* n_out);
+
+/* Number of kernel launches this context has enqueued since creation. */
+PANO_API unsigned long long pano_flow_launches(const pano_flow_ctx* ctx);
+
+/* ----------------------------------------------------------------------
+ * Stage entry points. Each runs one step of the path above on caller
+ * buffers with the same kernels pano_flow_pair / pano_blend_pair use, so
+ * each step can be checked and reused on its own. Float planes are
+ * row-major float32 with the given row pitch in elements.
+ * ---------------------------------------------------------------------- */
+
+/* Level 0 of the pyramid: unit-scaled luma Y (h x w) of an image (BT.601
+ * for c = 3, the sample itself for c = 1). Y pitch >= w. */
+PANO_API pano_status pano_stage_luma(const pano_image* in, float* Y, int y_pitch, void* cuda_stream);
+
+/* One pyramid REDUCE step (Section III-C-1, "LK pyramid"): [1 4 6 4 1]/16
+ * along y then x, replicate border, keep even rows and columns.
+ * src h x w -> dst ceil(h/2) x ceil(w/2). */
+PANO_API pano_status pano_stage_pyr_down(const float* src, int h, int w, int src_pitch, float* dst,
+                                int dst_pitch, void* cuda_stream);
+
+/* `iters` Lucas-Kanade steps at one level (Section III-C-1) on template T
+ * and target J (both h x w, same pitch), each step as described for
+ * pano_flow_pair: every pixel solves
+ *   (G(p) + lambda I) v = sum_{q in W(p)} grad T(q) (grad T(q) . u(q) - It(q)) + lambda u(p),
+ *   It(q) = J(q + u(q)) - T(q),  G(p) = sum_{q in W(p)} grad T grad T^T,
+ * over the (2r+1)^2 box W(p) clipped to the image, then sets u(p) = v.
+ * Starting flow: flow_in == NULL -> zero; upsample == 0 -> flow_in is an
+ * (h, w, 2) field used as is; upsample == 1 -> flow_in is the (in_h, in_w, 2)
+ * field of the next coarser level, and the start is 2 * flow_in sampled
+ * bilinearly at (x/2, y/2) (coarse-to-fine propagation).
+ * flow_out: (h, w, 2); it must not overlap flow_in. iters = 0 writes the
+ * starting flow. */
+PANO_API pano_status pano_stage_lk(const float* T, const float* J, int h, int w, int pitch,
+                          const float* flow_in, int in_h, int in_w, int upsample,
+                          float* flow_out, int iters, int radius, float lambda,
+                          void* cuda_stream);
+
+/* Bilinear flow warp, dst(p) = src(p + scale * flow(p)), per channel,
+ * clamp-to-edge; Code 1 evaluates it with scale = Blend for L and FlowRtoL
+ * and scale = 1 - Blend for R and FlowLtoR. dst: same h, w, c as src,
+ * dtype PANO_F32, unit-scaled values. */
+PANO_API pano_status pano_stage_warp(const pano_image* src, const float* flow, float scale,
+                            pano_image* dst, void* cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PANO_FLOW_H */

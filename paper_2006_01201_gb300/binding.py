@@ -1,0 +1,323 @@
+"""ctypes binding of ``libpanoflow.so`` (the C ABI in ``include/pano_flow.h``).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels. PyTorch supplies device memory (tensors) and streams. There is no
+fallback: if the library is missing, loading raises ``PanoError``.
+
+Tensor conventions
+  * an image is a CUDA tensor (H, W) or (H, W, C), C in {1, 3}, dtype uint8
+    or float32, whose channels and columns are contiguous (stride(-1) == 1
+    and stride(1) == C); any row stride is accepted;
+  * a flow is a contiguous float32 CUDA tensor (H, W, 2), [..., 0] = column
+    offset, [..., 1] = row offset; FlowAtoB lives on A's grid with
+    A(p) ~ B(p + FlowAtoB(p)).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Tuple
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpanoflow.so")
+
+PANO_OK, PANO_ERR_INVALID_ARG, PANO_ERR_UNSUPPORTED, PANO_ERR_OOM, PANO_ERR_CUDA, PANO_ERR_TIMEOUT = range(6)
+PANO_U8, PANO_F32, PANO_BF16, PANO_F16 = range(4)
+
+STATUS_NAMES = {0: "PANO_OK", 1: "PANO_ERR_INVALID_ARG", 2: "PANO_ERR_UNSUPPORTED", 3: "PANO_ERR_OOM",
+                4: "PANO_ERR_CUDA", 5: "PANO_ERR_TIMEOUT"}
+
+# Every function the header declares, with its ctypes signature.
+_VP, _I, _F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+
+
+class PanoImage(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("h", ctypes.c_int), ("w", ctypes.c_int), ("c", ctypes.c_int),
+                ("pitch_bytes", ctypes.c_size_t), ("dtype", ctypes.c_int)]
+
+
+class PanoParams(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("iters", ctypes.c_int), ("radius", ctypes.c_int),
+                ("lam", ctypes.c_float), ("soft_sharpness", ctypes.c_float),
+                ("flow_mag_coef", ctypes.c_float), ("pyr_dtype", ctypes.c_int)]
+
+
+class PanoTraceRecord(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("level", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
+_IMG = ctypes.POINTER(PanoImage)
+_PAR = ctypes.POINTER(PanoParams)
+
+PANO_TRACE_LUMA, PANO_TRACE_PYR_DOWN, PANO_TRACE_LK, PANO_TRACE_BLEND = 0x1, 0x2, 0x4, 0x8
+
+SIGNATURES = {
+    "pano_flow_params_default": ([_PAR], None),
+    "pano_flow_create": ([_PAR, _I, _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
+    "pano_flow_pair": ([_VP, _IMG, _IMG, _VP, _VP, _VP], _I),
+    "pano_blend_pair": ([_VP, _IMG, _IMG, _VP, _VP, _VP, _IMG, _VP], _I),
+    "pano_flow_destroy": ([_VP], _I),
+    "pano_last_error": ([_VP], ctypes.c_char_p),
+    "pano_trace_enable": ([_VP, ctypes.c_uint, _I], _I),
+    "pano_trace_read": ([_VP, ctypes.POINTER(PanoTraceRecord), _I, ctypes.POINTER(ctypes.c_int)], _I),
+    "pano_flow_launches": ([_VP], ctypes.c_ulonglong),
+    "pano_stage_luma": ([_IMG, _VP, _I, _VP], _I),
+    "pano_stage_pyr_down": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
+    "pano_stage_lk": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _VP], _I),
+    "pano_stage_warp": ([_IMG, _VP, _F, _IMG, _VP], _I),
+}
+
+_lib = None
+
+
+class PanoError(RuntimeError):
+    """A non-OK status from the library, or a missing library."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+        self.message = message
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise PanoError(-1, f"CUDA library not built: {path} is missing "
+                            "(run paper_2006_01201_gb300.build.build())")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(status: int) -> None:
+    if status != PANO_OK:
+        msg = load_library().pano_last_error(None)
+        raise PanoError(status, msg.decode() if msg else "")
+
+
+@dataclass
+class Params:
+    """Mirror of ``pano_flow_params`` (defaults: those of the library)."""
+
+    levels: int = 4
+    iters: int = 5
+    radius: int = 2
+    lam: float = 1e-2
+    soft_sharpness: float = 10.0
+    flow_mag_coef: float = 20.0
+
+    def to_c(self) -> PanoParams:
+        return PanoParams(self.levels, self.iters, self.radius, self.lam, self.soft_sharpness,
+                          self.flow_mag_coef, PANO_F32)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return int(s.cuda_stream)
+
+
+def image_desc(t) -> PanoImage:
+    """pano_image for an (H, W) or (H, W, C) CUDA tensor."""
+    torch = _torch()
+    if not t.is_cuda:
+        raise PanoError(PANO_ERR_INVALID_ARG, "image tensor must be on a CUDA device")
+    if t.dtype == torch.uint8:
+        dt, es = PANO_U8, 1
+    elif t.dtype == torch.float32:
+        dt, es = PANO_F32, 4
+    else:
+        raise PanoError(PANO_ERR_UNSUPPORTED, f"image dtype {t.dtype}")
+    if t.dim() == 2:
+        h, w, c = t.shape[0], t.shape[1], 1
+        ok = t.stride(1) == 1
+    elif t.dim() == 3:
+        h, w, c = t.shape
+        ok = t.stride(2) == 1 and t.stride(1) == c
+    else:
+        raise PanoError(PANO_ERR_INVALID_ARG, "image must be (H, W) or (H, W, C)")
+    if not ok:
+        raise PanoError(PANO_ERR_INVALID_ARG, "image columns and channels must be contiguous")
+    pitch = t.stride(0) * es if h > 1 else w * c * es
+    return PanoImage(t.data_ptr(), h, w, c, pitch, dt)
+
+
+def _flow_ptr(f, h, w, name) -> int:
+    torch = _torch()
+    if f.dtype != torch.float32 or not f.is_cuda or tuple(f.shape) != (h, w, 2) or not f.is_contiguous():
+        raise PanoError(PANO_ERR_INVALID_ARG, f"{name} must be a contiguous float32 CUDA tensor of shape {(h, w, 2)}")
+    return f.data_ptr()
+
+
+class FlowContext:
+    """A library context: scratch for strips up to max_h x max_w x max_c."""
+
+    def __init__(self, params: Optional[Params] = None, max_h: int = 4096, max_w: int = 4096, max_c: int = 3):
+        lib = load_library()
+        self.params = params or Params()
+        self.max_h, self.max_w, self.max_c = max_h, max_w, max_c
+        h = ctypes.c_void_p()
+        p = self.params.to_c()
+        _check(lib.pano_flow_create(ctypes.byref(p), max_h, max_w, max_c, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def handle(self) -> int:
+        return self._h.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load_library().pano_flow_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def flow_pair(self, L, R, out: Optional[Tuple] = None, stream=None):
+        """(FlowLtoR, FlowRtoL) of two strips, Section III-C-1."""
+        torch = _torch()
+        dl, dr = image_desc(L), image_desc(R)
+        h, w = dl.h, dl.w
+        if out is None:
+            out = (torch.empty((h, w, 2), dtype=torch.float32, device=L.device),
+                   torch.empty((h, w, 2), dtype=torch.float32, device=L.device))
+        lr = _flow_ptr(out[0], h, w, "flow_LtoR")
+        rl = _flow_ptr(out[1], h, w, "flow_RtoL")
+        _check(load_library().pano_flow_pair(self._h, ctypes.byref(dl), ctypes.byref(dr), lr, rl,
+                                             _stream_ptr(stream)))
+        return out
+
+    def blend_pair(self, L, R, flow_LtoR, flow_RtoL, blend=None, out=None, stream=None):
+        """F of Code 1 (Section III-C-3); blend None means the Eq. (1) strip ramp."""
+        torch = _torch()
+        dl, dr = image_desc(L), image_desc(R)
+        if out is None:
+            out = torch.empty_like(L)
+        df = image_desc(out)
+        bp = None
+        if blend is not None:
+            if blend.dtype != torch.float32 or not blend.is_contiguous() or tuple(blend.shape) != (dl.h, dl.w):
+                raise PanoError(PANO_ERR_INVALID_ARG, "blend must be a contiguous float32 (H, W) tensor")
+            bp = blend.data_ptr()
+        _check(load_library().pano_blend_pair(
+            self._h, ctypes.byref(dl), ctypes.byref(dr), _flow_ptr(flow_LtoR, dl.h, dl.w, "flow_LtoR"),
+            _flow_ptr(flow_RtoL, dl.h, dl.w, "flow_RtoL"), bp, ctypes.byref(df), _stream_ptr(stream)))
+        return out
+
+    def stitch_pair(self, L, R, stream=None):
+        """flow_pair followed by blend_pair; returns (FlowLtoR, FlowRtoL, F)."""
+        lr, rl = self.flow_pair(L, R, stream=stream)
+        return lr, rl, self.blend_pair(L, R, lr, rl, stream=stream)
+
+    def stitch_host(self, L_host, R_host, F_host, work, stream=None):
+        """Whole path from host strips to a host F on one stream.
+
+        L_host, R_host, F_host: CPU tensors (pinned for asynchronous copies).
+        work: dict of preallocated device tensors ``L``, ``R``, ``lr``, ``rl``,
+        ``F`` of matching shapes. Enqueues H2D copies, flow_pair, blend_pair
+        and the D2H copy of F; returns without synchronising.
+        """
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            work["L"].copy_(L_host, non_blocking=True)
+            work["R"].copy_(R_host, non_blocking=True)
+            self.flow_pair(work["L"], work["R"], out=(work["lr"], work["rl"]), stream=s)
+            self.blend_pair(work["L"], work["R"], work["lr"], work["rl"], out=work["F"], stream=s)
+            F_host.copy_(work["F"], non_blocking=True)
+        return F_host
+
+    # -- tracing -------------------------------------------------------------
+
+    def trace_enable(self, kind_mask: int, capacity: int) -> None:
+        """Bracket launches of the selected kinds with CUDA events."""
+        _check(load_library().pano_trace_enable(self._h, kind_mask, capacity))
+
+    def trace_read(self, max_records: int = 4096):
+        """[(kind, level, ms), ...] of the launches recorded since the last read."""
+        buf = (PanoTraceRecord * max_records)()
+        n = ctypes.c_int()
+        _check(load_library().pano_trace_read(self._h, buf, max_records, ctypes.byref(n)))
+        return [(buf[i].kind, buf[i].level, buf[i].ms) for i in range(n.value)]
+
+    @property
+    def launches(self) -> int:
+        """Kernel launches enqueued by this context so far."""
+        return int(load_library().pano_flow_launches(self._h))
+
+
+# ---------------------------------------------------------------------------
+# Stage entry points
+# ---------------------------------------------------------------------------
+
+def stage_luma(img, stream=None):
+    torch = _torch()
+    d = image_desc(img)
+    Y = torch.empty((d.h, d.w), dtype=torch.float32, device=img.device)
+    _check(load_library().pano_stage_luma(ctypes.byref(d), Y.data_ptr(), d.w, _stream_ptr(stream)))
+    return Y
+
+
+def stage_pyr_down(src, stream=None):
+    torch = _torch()
+    if src.dtype != torch.float32 or src.dim() != 2 or src.stride(1) != 1:
+        raise PanoError(PANO_ERR_INVALID_ARG, "src must be a float32 (H, W) tensor with contiguous rows")
+    h, w = src.shape
+    dst = torch.empty(((h + 1) // 2, (w + 1) // 2), dtype=torch.float32, device=src.device)
+    _check(load_library().pano_stage_pyr_down(src.data_ptr(), h, w, src.stride(0), dst.data_ptr(),
+                                              dst.stride(0), _stream_ptr(stream)))
+    return dst
+
+
+def stage_lk(T, J, flow_in=None, upsample=False, iters=5, radius=2, lam=1e-2, stream=None):
+    torch = _torch()
+    for t, n in ((T, "T"), (J, "J")):
+        if t.dtype != torch.float32 or t.dim() != 2 or not t.is_contiguous():
+            raise PanoError(PANO_ERR_INVALID_ARG, f"{n} must be a contiguous float32 (H, W) tensor")
+    h, w = T.shape
+    if tuple(J.shape) != (h, w):
+        raise PanoError(PANO_ERR_INVALID_ARG, "T and J differ in size")
+    out = torch.empty((h, w, 2), dtype=torch.float32, device=T.device)
+    fin, ih, iw = None, 0, 0
+    if flow_in is not None:
+        if flow_in.dtype != torch.float32 or not flow_in.is_contiguous() or flow_in.dim() != 3:
+            raise PanoError(PANO_ERR_INVALID_ARG, "flow_in must be a contiguous float32 (h, w, 2) tensor")
+        ih, iw = flow_in.shape[0], flow_in.shape[1]
+        if not upsample and (ih, iw) != (h, w):
+            raise PanoError(PANO_ERR_INVALID_ARG, "flow_in must match T unless upsample is set")
+        fin = flow_in.data_ptr()
+    _check(load_library().pano_stage_lk(T.data_ptr(), J.data_ptr(), h, w, w, fin, ih, iw, int(bool(upsample)),
+                                        out.data_ptr(), iters, radius, lam, _stream_ptr(stream)))
+    return out
+
+
+def stage_warp(src, flow, scale=1.0, stream=None):
+    torch = _torch()
+    d = image_desc(src)
+    dst = torch.empty(src.shape, dtype=torch.float32, device=src.device)
+    dd = image_desc(dst)
+    _check(load_library().pano_stage_warp(ctypes.byref(d), _flow_ptr(flow, d.h, d.w, "flow"), float(scale),
+                                          ctypes.byref(dd), _stream_ptr(stream)))
+    return dst

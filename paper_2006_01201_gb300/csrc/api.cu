@@ -1,0 +1,557 @@
+// api.cu -- the C ABI declared in include/pano_flow.h: argument checks, the
+// context (scratch pyramids and coarse flows), and the launch sequence of the
+// blend path of Section III-C:
+//   pano_flow_pair : luma (level 0) -> REDUCE x (levels-1) -> LK level
+//                    (both directions per launch) from coarse to fine
+//   pano_blend_pair: Code 1 with Eq. (1)
+// Every call only enqueues kernels on the caller's stream.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <climits>
+#include <new>
+
+#include "common.cuh"
+#include "pano_flow.h"
+
+using namespace pano;
+
+struct pano_flow_ctx {
+    pano_flow_params p;
+    int max_h, max_w, max_c;
+    int device;
+    int nlev;
+    int lev_h[kMaxLevels], lev_w[kMaxLevels];  // level sizes at the maximum strip size
+    int lev_pitch[kMaxLevels];                 // floats
+    int flow_pitch[kMaxLevels];                // float2 elements
+    float* pyr[2][kMaxLevels];                 // luma pyramids of L and R
+    float* flw[2][kMaxLevels];                 // flows of levels >= 1, per direction
+    void* buf;
+    size_t buf_bytes;
+    int tile_w, tile_h;
+    unsigned long long launches;
+    // tracing
+    unsigned trace_mask;
+    int trace_cap, trace_n;
+    cudaEvent_t* ev;  // 2 * trace_cap events: start, stop per record
+    pano_trace_record* rec;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+pano_status fail(pano_status st, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+pano_status cuda_fail(cudaError_t e, const char* what) {
+    return fail(PANO_ERR_CUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int elem_size(int dtype) { return dtype == PANO_U8 ? 1 : (dtype == PANO_F32 ? 4 : 2); }
+
+pano_status check_image(const pano_image* im, const char* name) {
+    if (!im) return fail(PANO_ERR_INVALID_ARG, "%s is NULL", name);
+    if (!im->data) return fail(PANO_ERR_INVALID_ARG, "%s->data is NULL", name);
+    if (im->h < 1 || im->w < 1) return fail(PANO_ERR_INVALID_ARG, "%s size %dx%d", name, im->h, im->w);
+    if (im->dtype == PANO_BF16 || im->dtype == PANO_F16)
+        return fail(PANO_ERR_UNSUPPORTED, "%s: 16-bit images are not supported", name);
+    if (im->dtype != PANO_U8 && im->dtype != PANO_F32)
+        return fail(PANO_ERR_INVALID_ARG, "%s: unknown dtype %d", name, im->dtype);
+    if (im->c != 1 && im->c != 3)
+        return fail(PANO_ERR_UNSUPPORTED, "%s: %d channels (1 or 3 supported)", name, im->c);
+    size_t es = (size_t)elem_size(im->dtype);
+    if (im->pitch_bytes < (size_t)im->w * im->c * es)
+        return fail(PANO_ERR_INVALID_ARG, "%s: pitch %zu < row size %zu", name, im->pitch_bytes,
+                    (size_t)im->w * im->c * es);
+    if (im->pitch_bytes % es || ((uintptr_t)im->data) % es)
+        return fail(PANO_ERR_INVALID_ARG, "%s: pitch or data not aligned to the element size", name);
+    if ((double)im->h * (double)(im->pitch_bytes / es) > (double)INT_MAX)
+        return fail(PANO_ERR_UNSUPPORTED, "%s: more than 2^31 elements", name);
+    return PANO_OK;
+}
+
+pano_status check_same(const pano_image* a, const pano_image* b, const char* na, const char* nb) {
+    if (a->h != b->h || a->w != b->w || a->c != b->c || a->dtype != b->dtype)
+        return fail(PANO_ERR_INVALID_ARG, "%s and %s differ in size, channels or dtype", na, nb);
+    return PANO_OK;
+}
+
+pano_status check_flow(const void* f, const char* name) {
+    if (!f) return fail(PANO_ERR_INVALID_ARG, "%s is NULL", name);
+    if (((uintptr_t)f) % 8) return fail(PANO_ERR_INVALID_ARG, "%s is not 8-byte aligned", name);
+    return PANO_OK;
+}
+
+bool overlaps(const void* a, size_t na, const void* b, size_t nb) {
+    uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+    return x < y + nb && y < x + na;
+}
+
+pano_status check_params(const pano_flow_params* p) {
+    if (!p) return fail(PANO_ERR_INVALID_ARG, "params is NULL");
+    if (p->levels < 1 || p->levels > kMaxLevels)
+        return fail(PANO_ERR_INVALID_ARG, "levels %d not in 1..%d", p->levels, kMaxLevels);
+    if (p->iters < 0 || p->iters > 16) return fail(PANO_ERR_INVALID_ARG, "iters %d not in 0..16", p->iters);
+    if (p->radius < 1 || p->radius > 3) return fail(PANO_ERR_INVALID_ARG, "radius %d not in 1..3", p->radius);
+    if (!(p->lambda >= 0.f) || !(p->lambda < 1e30f))
+        return fail(PANO_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    if (!(p->soft_sharpness == p->soft_sharpness) || !(p->flow_mag_coef == p->flow_mag_coef))
+        return fail(PANO_ERR_INVALID_ARG, "softmax parameters must not be NaN");
+    if (p->pyr_dtype != PANO_F32) return fail(PANO_ERR_UNSUPPORTED, "pyramid dtype %d (only PANO_F32)", p->pyr_dtype);
+    return PANO_OK;
+}
+
+int max_optin_smem() {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return -1;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return -1;
+    return v;
+}
+
+// Largest tile from a fixed list whose shared-memory footprint fits.
+bool pick_tile(int iters, int radius, int max_smem, int* tw, int* th) {
+    static const int cand[][2] = {{32, 16}, {32, 8}, {16, 16}, {16, 8}, {8, 8}};
+    for (auto& c : cand) {
+        if (lk_smem_bytes(c[0], c[1], iters, radius) <= (size_t)max_smem) {
+            *tw = c[0];
+            *th = c[1];
+            return true;
+        }
+    }
+    return false;
+}
+
+// Sets the dynamic shared-memory limit of the LK kernel once per device.
+pano_status ensure_lk_ready(int* max_smem_out) {
+    static int prepared[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    int ms = max_optin_smem();
+    if (ms <= 0) return fail(PANO_ERR_CUDA, "cannot query the shared-memory limit");
+    if (dev >= 0 && dev < 64 && !prepared[dev]) {
+        if ((e = lk_prepare(ms)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        prepared[dev] = 1;
+    }
+    *max_smem_out = ms;
+    return PANO_OK;
+}
+
+void trace_free(pano_flow_ctx* c) {
+    if (c->ev) {
+        for (int i = 0; i < 2 * c->trace_cap; ++i)
+            if (c->ev[i]) cudaEventDestroy(c->ev[i]);
+        delete[] c->ev;
+    }
+    delete[] c->rec;
+    c->ev = nullptr;
+    c->rec = nullptr;
+    c->trace_cap = c->trace_n = 0;
+    c->trace_mask = 0;
+}
+
+// Brackets one launch with events when its kind is traced; returns the slot.
+int trace_begin(pano_flow_ctx* c, unsigned kind, int level, cudaStream_t s) {
+    if (!(c->trace_mask & kind) || c->trace_n >= c->trace_cap) return -1;
+    int i = c->trace_n++;
+    c->rec[i].kind = (int)kind;
+    c->rec[i].level = level;
+    c->rec[i].ms = 0.f;
+    cudaEventRecord(c->ev[2 * i], s);
+    return i;
+}
+
+void trace_end(pano_flow_ctx* c, int slot, cudaStream_t s) {
+    if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], s);
+}
+
+ImageDesc desc(const pano_image* im) {
+    ImageDesc d;
+    d.data = im->data;
+    d.h = im->h;
+    d.w = im->w;
+    d.c = im->c;
+    d.pitch_bytes = (long long)im->pitch_bytes;
+    d.dtype = im->dtype == PANO_U8 ? 0 : 1;
+    return d;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pano_flow_params_default(pano_flow_params* p) {
+    if (!p) return;
+    p->levels = 4;
+    p->iters = 5;
+    p->radius = 2;
+    p->lambda = 1e-2f;
+    p->soft_sharpness = 10.0f;
+    p->flow_mag_coef = 20.0f;
+    p->pyr_dtype = PANO_F32;
+}
+
+const char* pano_last_error(const pano_flow_ctx*) { return g_err; }
+
+pano_status pano_flow_create(const pano_flow_params* p, int max_h, int max_w, int max_c,
+                             pano_flow_ctx** out) {
+    if (!out) return fail(PANO_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    pano_status st = check_params(p);
+    if (st != PANO_OK) return st;
+    if (max_h < 1 || max_w < 1) return fail(PANO_ERR_INVALID_ARG, "max size %dx%d", max_h, max_w);
+    if (max_c != 1 && max_c != 3) return fail(PANO_ERR_INVALID_ARG, "max_c %d (1 or 3)", max_c);
+    if ((double)max_h * (double)align_up((size_t)max_w * 3, 64) > (double)INT_MAX)
+        return fail(PANO_ERR_UNSUPPORTED, "strip too large for 32-bit offsets");
+    int max_smem = 0;
+    if ((st = ensure_lk_ready(&max_smem)) != PANO_OK) return st;
+    int tw = 0, th = 0;
+    if (!pick_tile(p->iters, p->radius, max_smem, &tw, &th))
+        return fail(PANO_ERR_UNSUPPORTED, "iters * radius = %d needs more shared memory than the device has",
+                    p->iters * p->radius);
+
+    pano_flow_ctx* c = new (std::nothrow) pano_flow_ctx;
+    if (!c) return fail(PANO_ERR_OOM, "host allocation failed");
+    memset(c, 0, sizeof(*c));
+    c->p = *p;
+    c->max_h = max_h;
+    c->max_w = max_w;
+    c->max_c = max_c;
+    c->nlev = p->levels;
+    c->tile_w = tw;
+    c->tile_h = th;
+    cudaGetDevice(&c->device);
+    size_t off[2][2][kMaxLevels];
+    size_t total = 0;
+    for (int l = 0; l < c->nlev; ++l) {
+        c->lev_h[l] = l == 0 ? max_h : (c->lev_h[l - 1] + 1) / 2;
+        c->lev_w[l] = l == 0 ? max_w : (c->lev_w[l - 1] + 1) / 2;
+        c->lev_pitch[l] = (int)align_up(c->lev_w[l], 32);
+        c->flow_pitch[l] = (int)align_up(c->lev_w[l], 16);
+    }
+    for (int s = 0; s < 2; ++s)
+        for (int l = 0; l < c->nlev; ++l) {
+            off[0][s][l] = total;
+            total += align_up((size_t)c->lev_pitch[l] * c->lev_h[l] * sizeof(float), 256);
+        }
+    for (int d = 0; d < 2; ++d)
+        for (int l = 1; l < c->nlev; ++l) {
+            off[1][d][l] = total;
+            total += align_up((size_t)c->flow_pitch[l] * c->lev_h[l] * sizeof(float2), 256);
+        }
+    cudaError_t e = cudaMalloc(&c->buf, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(PANO_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
+    }
+    c->buf_bytes = total;
+    char* b = static_cast<char*>(c->buf);
+    for (int s = 0; s < 2; ++s)
+        for (int l = 0; l < c->nlev; ++l) c->pyr[s][l] = reinterpret_cast<float*>(b + off[0][s][l]);
+    for (int d = 0; d < 2; ++d)
+        for (int l = 1; l < c->nlev; ++l) c->flw[d][l] = reinterpret_cast<float*>(b + off[1][d][l]);
+    *out = c;
+    return PANO_OK;
+}
+
+pano_status pano_flow_destroy(pano_flow_ctx* c) {
+    if (!c) return PANO_OK;
+    trace_free(c);
+    cudaError_t e = c->buf ? cudaFree(c->buf) : cudaSuccess;
+    delete c;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
+    return PANO_OK;
+}
+
+pano_status pano_flow_pair(pano_flow_ctx* c, const pano_image* L, const pano_image* R,
+                           float* flow_LtoR, float* flow_RtoL, void* cuda_stream) {
+    if (!c) return fail(PANO_ERR_INVALID_ARG, "context is NULL");
+    pano_status st;
+    if ((st = check_image(L, "L")) != PANO_OK) return st;
+    if ((st = check_image(R, "R")) != PANO_OK) return st;
+    if ((st = check_same(L, R, "L", "R")) != PANO_OK) return st;
+    if ((st = check_flow(flow_LtoR, "flow_LtoR")) != PANO_OK) return st;
+    if ((st = check_flow(flow_RtoL, "flow_RtoL")) != PANO_OK) return st;
+    if (L->h > c->max_h || L->w > c->max_w || L->c > c->max_c)
+        return fail(PANO_ERR_INVALID_ARG, "strip %dx%dx%d exceeds the context maximum %dx%dx%d", L->h, L->w,
+                    L->c, c->max_h, c->max_w, c->max_c);
+    const size_t fbytes = (size_t)L->h * L->w * 2 * sizeof(float);
+    if (overlaps(flow_LtoR, fbytes, flow_RtoL, fbytes)) return fail(PANO_ERR_INVALID_ARG, "the two flows overlap");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const int nlev = c->nlev;
+    int hs[kMaxLevels], ws[kMaxLevels];
+    hs[0] = L->h;
+    ws[0] = L->w;
+    for (int l = 1; l < nlev; ++l) {
+        hs[l] = (hs[l - 1] + 1) / 2;
+        ws[l] = (ws[l - 1] + 1) / 2;
+    }
+    // Level-0 planes: a one-channel float strip is its own luma.
+    const float* plane[2][kMaxLevels];
+    int ppitch[2][kMaxLevels];
+    const pano_image* img[2] = {L, R};
+    LumaArgs la;
+    memset(&la, 0, sizeof(la));
+    for (int si = 0; si < 2; ++si) {
+        for (int l = 0; l < nlev; ++l) {
+            plane[si][l] = c->pyr[si][l];
+            ppitch[si][l] = c->lev_pitch[l];
+        }
+        if (img[si]->dtype == PANO_F32 && img[si]->c == 1) {
+            plane[si][0] = static_cast<const float*>(img[si]->data);
+            ppitch[si][0] = (int)(img[si]->pitch_bytes / sizeof(float));
+        } else {
+            la.in[la.count] = desc(img[si]);
+            la.out[la.count] = c->pyr[si][0];
+            la.out_pitch[la.count] = c->lev_pitch[0];
+            la.count++;
+        }
+    }
+    cudaError_t e;
+    if (la.count > 0) {
+        int t = trace_begin(c, PANO_TRACE_LUMA, 0, s);
+        if ((e = launch_luma(la, s)) != cudaSuccess) return cuda_fail(e, "luma launch");
+        trace_end(c, t, s);
+        c->launches++;
+    }
+    for (int l = 1; l < nlev; ++l) {
+        PyrDownArgs pa;
+        memset(&pa, 0, sizeof(pa));
+        for (int si = 0; si < 2; ++si) {
+            pa.src[si] = plane[si][l - 1];
+            pa.src_pitch[si] = ppitch[si][l - 1];
+            pa.dst[si] = c->pyr[si][l];
+            pa.dst_pitch[si] = c->lev_pitch[l];
+        }
+        pa.h = hs[l - 1];
+        pa.w = ws[l - 1];
+        pa.count = 2;
+        int t = trace_begin(c, PANO_TRACE_PYR_DOWN, l, s);
+        if ((e = launch_pyr_down(pa, s)) != cudaSuccess) return cuda_fail(e, "pyramid launch");
+        trace_end(c, t, s);
+        c->launches++;
+    }
+    float* out[2] = {flow_LtoR, flow_RtoL};
+    for (int l = nlev - 1; l >= 0; --l) {
+        LkArgs ka;
+        memset(&ka, 0, sizeof(ka));
+        for (int d = 0; d < 2; ++d) {
+            // direction 0: FlowLtoR (template L, target R); 1: FlowRtoL
+            ka.dir[d].T = plane[d][l];
+            ka.dir[d].pitchT = ppitch[d][l];
+            ka.dir[d].J = plane[1 - d][l];
+            ka.dir[d].pitchJ = ppitch[1 - d][l];
+            ka.dir[d].uin = l == nlev - 1 ? nullptr : c->flw[d][l + 1];
+            ka.dir[d].uin_pitch = l == nlev - 1 ? 0 : c->flow_pitch[l + 1];
+            ka.dir[d].uout = l == 0 ? out[d] : c->flw[d][l];
+            ka.dir[d].uout_pitch = l == 0 ? ws[0] : c->flow_pitch[l];
+        }
+        ka.h = hs[l];
+        ka.w = ws[l];
+        ka.in_h = l == nlev - 1 ? 0 : hs[l + 1];
+        ka.in_w = l == nlev - 1 ? 0 : ws[l + 1];
+        ka.mode = l == nlev - 1 ? 0 : 1;
+        ka.iters = c->p.iters;
+        ka.radius = c->p.radius;
+        ka.lambda = c->p.lambda;
+        ka.tile_w = c->tile_w;
+        ka.tile_h = c->tile_h;
+        int t = trace_begin(c, PANO_TRACE_LK, l, s);
+        if ((e = launch_lk_level(ka, 2, s)) != cudaSuccess) return cuda_fail(e, "LK launch");
+        trace_end(c, t, s);
+        c->launches++;
+    }
+    return PANO_OK;
+}
+
+pano_status pano_blend_pair(pano_flow_ctx* c, const pano_image* L, const pano_image* R,
+                            const float* flow_LtoR, const float* flow_RtoL, const float* blend,
+                            pano_image* F, void* cuda_stream) {
+    if (!c) return fail(PANO_ERR_INVALID_ARG, "context is NULL");
+    pano_status st;
+    if ((st = check_image(L, "L")) != PANO_OK) return st;
+    if ((st = check_image(R, "R")) != PANO_OK) return st;
+    if ((st = check_image(F, "F")) != PANO_OK) return st;
+    if ((st = check_same(L, R, "L", "R")) != PANO_OK) return st;
+    if ((st = check_same(L, F, "L", "F")) != PANO_OK) return st;
+    if ((st = check_flow(flow_LtoR, "flow_LtoR")) != PANO_OK) return st;
+    if ((st = check_flow(flow_RtoL, "flow_RtoL")) != PANO_OK) return st;
+    if (blend && ((uintptr_t)blend) % 4) return fail(PANO_ERR_INVALID_ARG, "blend is not 4-byte aligned");
+    const size_t fb = (size_t)F->h * F->pitch_bytes;
+    if (overlaps(F->data, fb, L->data, (size_t)L->h * L->pitch_bytes) ||
+        overlaps(F->data, fb, R->data, (size_t)R->h * R->pitch_bytes))
+        return fail(PANO_ERR_INVALID_ARG, "F overlaps an input strip");
+    BlendArgs a;
+    a.L = desc(L);
+    a.R = desc(R);
+    a.flowLR = reinterpret_cast<const float2*>(flow_LtoR);
+    a.flowRL = reinterpret_cast<const float2*>(flow_RtoL);
+    a.blend = blend;
+    a.F = F->data;
+    a.F_pitch_bytes = (long long)F->pitch_bytes;
+    a.k_sharp = c->p.soft_sharpness;
+    a.k_mag = c->p.flow_mag_coef;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    int t = trace_begin(c, PANO_TRACE_BLEND, 0, s);
+    cudaError_t e = launch_blend(a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "blend launch");
+    trace_end(c, t, s);
+    c->launches++;
+    return PANO_OK;
+}
+
+pano_status pano_trace_enable(pano_flow_ctx* c, unsigned kind_mask, int capacity) {
+    if (!c) return fail(PANO_ERR_INVALID_ARG, "context is NULL");
+    if (capacity < 0 || capacity > (1 << 20)) return fail(PANO_ERR_INVALID_ARG, "capacity %d", capacity);
+    trace_free(c);
+    if (capacity == 0 || kind_mask == 0) return PANO_OK;
+    c->ev = new (std::nothrow) cudaEvent_t[2 * (size_t)capacity]();
+    c->rec = new (std::nothrow) pano_trace_record[capacity];
+    if (!c->ev || !c->rec) {
+        delete[] c->ev;
+        delete[] c->rec;
+        c->ev = nullptr;
+        c->rec = nullptr;
+        return fail(PANO_ERR_OOM, "host allocation failed");
+    }
+    c->trace_cap = capacity;
+    for (int i = 0; i < 2 * capacity; ++i) {
+        cudaError_t e = cudaEventCreate(&c->ev[i]);
+        if (e != cudaSuccess) {
+            trace_free(c);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    c->trace_mask = kind_mask;
+    c->trace_n = 0;
+    return PANO_OK;
+}
+
+pano_status pano_trace_read(pano_flow_ctx* c, pano_trace_record* out, int max_records, int* n_out) {
+    if (!c || !n_out || (max_records > 0 && !out)) return fail(PANO_ERR_INVALID_ARG, "NULL argument");
+    *n_out = 0;
+    int n = c->trace_n < max_records ? c->trace_n : max_records;
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = cudaEventSynchronize(c->ev[2 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&c->rec[i].ms, c->ev[2 * i], c->ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "reading trace events");
+        out[i] = c->rec[i];
+    }
+    *n_out = n;
+    c->trace_n = 0;
+    return PANO_OK;
+}
+
+unsigned long long pano_flow_launches(const pano_flow_ctx* c) { return c ? c->launches : 0ull; }
+
+// ---------------------------------------------------------------------------
+// Stage entry points
+// ---------------------------------------------------------------------------
+
+pano_status pano_stage_luma(const pano_image* in, float* Y, int y_pitch, void* cuda_stream) {
+    pano_status st;
+    if ((st = check_image(in, "in")) != PANO_OK) return st;
+    if (!Y || ((uintptr_t)Y) % 4) return fail(PANO_ERR_INVALID_ARG, "Y is NULL or misaligned");
+    if (y_pitch < in->w) return fail(PANO_ERR_INVALID_ARG, "y_pitch %d < w %d", y_pitch, in->w);
+    LumaArgs la;
+    memset(&la, 0, sizeof(la));
+    la.in[0] = desc(in);
+    la.out[0] = Y;
+    la.out_pitch[0] = y_pitch;
+    la.count = 1;
+    cudaError_t e = launch_luma(la, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? PANO_OK : cuda_fail(e, "luma launch");
+}
+
+pano_status pano_stage_pyr_down(const float* src, int h, int w, int src_pitch, float* dst, int dst_pitch,
+                                void* cuda_stream) {
+    if (!src || !dst || ((uintptr_t)src) % 4 || ((uintptr_t)dst) % 4)
+        return fail(PANO_ERR_INVALID_ARG, "src or dst NULL or misaligned");
+    if (h < 1 || w < 1 || src_pitch < w || dst_pitch < (w + 1) / 2)
+        return fail(PANO_ERR_INVALID_ARG, "bad size or pitch");
+    PyrDownArgs pa;
+    memset(&pa, 0, sizeof(pa));
+    pa.src[0] = src;
+    pa.dst[0] = dst;
+    pa.src_pitch[0] = src_pitch;
+    pa.dst_pitch[0] = dst_pitch;
+    pa.h = h;
+    pa.w = w;
+    pa.count = 1;
+    cudaError_t e = launch_pyr_down(pa, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? PANO_OK : cuda_fail(e, "pyramid launch");
+}
+
+pano_status pano_stage_lk(const float* T, const float* J, int h, int w, int pitch, const float* flow_in,
+                          int in_h, int in_w, int upsample, float* flow_out, int iters, int radius,
+                          float lambda, void* cuda_stream) {
+    if (!T || !J || ((uintptr_t)T) % 4 || ((uintptr_t)J) % 4)
+        return fail(PANO_ERR_INVALID_ARG, "T or J NULL or misaligned");
+    if (h < 1 || w < 1 || pitch < w) return fail(PANO_ERR_INVALID_ARG, "bad size or pitch");
+    pano_status st;
+    if ((st = check_flow(flow_out, "flow_out")) != PANO_OK) return st;
+    if (flow_in && ((uintptr_t)flow_in) % 8) return fail(PANO_ERR_INVALID_ARG, "flow_in is not 8-byte aligned");
+    if (iters < 0 || iters > 16 || radius < 1 || radius > 3 || !(lambda >= 0.f))
+        return fail(PANO_ERR_INVALID_ARG, "iters, radius or lambda out of range");
+    int ih = h, iw = w;
+    if (flow_in && upsample) {
+        if (in_h < 1 || in_w < 1) return fail(PANO_ERR_INVALID_ARG, "coarse flow size %dx%d", in_h, in_w);
+        ih = in_h;
+        iw = in_w;
+    }
+    if (flow_in && overlaps(flow_in, (size_t)ih * iw * 8, flow_out, (size_t)h * w * 8))
+        return fail(PANO_ERR_INVALID_ARG, "flow_in and flow_out overlap");
+    int max_smem = 0;
+    if ((st = ensure_lk_ready(&max_smem)) != PANO_OK) return st;
+    LkArgs ka;
+    memset(&ka, 0, sizeof(ka));
+    if (!pick_tile(iters, radius, max_smem, &ka.tile_w, &ka.tile_h))
+        return fail(PANO_ERR_UNSUPPORTED, "iters * radius too large for shared memory");
+    ka.dir[0].T = T;
+    ka.dir[0].J = J;
+    ka.dir[0].pitchT = ka.dir[0].pitchJ = pitch;
+    ka.dir[0].uin = flow_in;
+    ka.dir[0].uin_pitch = iw;
+    ka.dir[0].uout = flow_out;
+    ka.dir[0].uout_pitch = w;
+    ka.h = h;
+    ka.w = w;
+    ka.in_h = ih;
+    ka.in_w = iw;
+    ka.mode = flow_in ? (upsample ? 1 : 2) : 0;
+    ka.iters = iters;
+    ka.radius = radius;
+    ka.lambda = lambda;
+    cudaError_t e = launch_lk_level(ka, 1, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? PANO_OK : cuda_fail(e, "LK launch");
+}
+
+pano_status pano_stage_warp(const pano_image* src, const float* flow, float scale, pano_image* dst,
+                            void* cuda_stream) {
+    pano_status st;
+    if ((st = check_image(src, "src")) != PANO_OK) return st;
+    if ((st = check_image(dst, "dst")) != PANO_OK) return st;
+    if ((st = check_flow(flow, "flow")) != PANO_OK) return st;
+    if (dst->dtype != PANO_F32 || dst->h != src->h || dst->w != src->w || dst->c != src->c)
+        return fail(PANO_ERR_INVALID_ARG, "dst must be float32 with the size and channels of src");
+    WarpArgs a;
+    a.src = desc(src);
+    a.flow = reinterpret_cast<const float2*>(flow);
+    a.scale = scale;
+    a.dst = static_cast<float*>(dst->data);
+    a.dst_pitch_bytes = (long long)dst->pitch_bytes;
+    cudaError_t e = launch_warp(a, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? PANO_OK : cuda_fail(e, "warp launch");
+}
+
+}  // extern "C"

@@ -1,0 +1,107 @@
+// blend.cu -- the asymmetric softmax blend of Code 1 (Section III-C-3) with
+// the global blending coefficient of Eq. (1) (Section III-C-2), and the plain
+// bilinear flow warp.
+//
+// Code 1, Area3 branch, at pixel p = (x, y) of the overlap strips:
+//   BlendL = 1 - Blend(p), BlendR = Blend(p)
+//   ColorL = L(p + (1 - BlendL) FlowRtoL(p)),  ColorR = R(p + (1 - BlendR) FlowLtoR(p))
+//   FlowL = 1 + kFlowMagCoef FlowMagRL,  FlowR = 1 + kFlowMagCoef FlowMagLR
+//   F = (ColorL e^{k BlendL FlowL} + ColorR e^{k BlendR FlowR}) / (e^{k BlendL FlowL} + e^{k BlendR FlowR})
+// FlowMagRL / FlowMagLR are |FlowRtoL(p)| / w and |FlowLtoR(p)| / w. With no
+// Blend array the strip value of Eq. (1) is used, (x + 1) / (w + 1). The
+// softmax is evaluated as the equal logistic form 1 / (1 + e^{sR - sL}).
+#include "common.cuh"
+
+namespace pano {
+
+namespace {
+
+// Bilinear sample of channel k of an interleaved image, raw sample scale
+// (0..255 for u8, as stored for f32).
+template <typename Tv>
+__device__ __forceinline__ float sample_channel(const Tv* __restrict__ base, const Taps& t, int k) {
+    return bilinear_mix(t, (float)base[t.o00 + k], (float)base[t.o10 + k], (float)base[t.o01 + k],
+                        (float)base[t.o11 + k]);
+}
+
+template <typename Tv, int C>
+__device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y) {
+    const int w = a.L.w, h = a.L.h;
+    const long long p = (long long)y * w + x;
+    const float B = a.blend ? a.blend[p] : (float)(x + 1) / (float)(w + 1);
+    const float2 rl = a.flowRL[p], lr = a.flowLR[p];
+    const float blendL = 1.f - B, blendR = B;
+    // ColorL at p + (1 - BlendL) FlowRtoL, ColorR at p + (1 - BlendR) FlowLtoR
+    const int pitchL = (int)(a.L.pitch_bytes / sizeof(Tv)), pitchR = (int)(a.R.pitch_bytes / sizeof(Tv));
+    const Taps tl = bilinear_taps(x, y, (1.f - blendL) * rl.x, (1.f - blendL) * rl.y, w, h, pitchL, C);
+    const Taps tr = bilinear_taps(x, y, (1.f - blendR) * lr.x, (1.f - blendR) * lr.y, w, h, pitchR, C);
+    const float magRL = sqrtf(fmaf(rl.x, rl.x, rl.y * rl.y)) / (float)w;
+    const float magLR = sqrtf(fmaf(lr.x, lr.x, lr.y * lr.y)) / (float)w;
+    const float sL = a.k_sharp * blendL * fmaf(a.k_mag, magRL, 1.f);
+    const float sR = a.k_sharp * blendR * fmaf(a.k_mag, magLR, 1.f);
+    const float e = expf(fminf(fmaxf(sR - sL, -80.f), 80.f));
+    const float wL = 1.f / (1.f + e);
+    const float wR = e * wL;
+    const Tv* __restrict__ Lb = static_cast<const Tv*>(a.L.data);
+    const Tv* __restrict__ Rb = static_cast<const Tv*>(a.R.data);
+    Tv* out = reinterpret_cast<Tv*>(static_cast<char*>(a.F) + (long long)y * a.F_pitch_bytes) + x * C;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        const float cl = sample_channel(Lb, tl, k);
+        const float cr = sample_channel(Rb, tr, k);
+        const float f = fmaf(cl, wL, cr * wR);
+        if constexpr (sizeof(Tv) == 1) {
+            out[k] = (Tv)min(max(__float2int_rn(f), 0), 255);
+        } else {
+            out[k] = (Tv)f;
+        }
+    }
+}
+
+template <typename Tv, int C>
+__global__ void __launch_bounds__(256) blend_kernel(BlendArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.L.w || y >= a.L.h) return;
+    blend_pixel<Tv, C>(a, x, y);
+}
+
+template <typename Tv>
+__global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int w = a.src.w, h = a.src.h, C = a.src.c;
+    if (x >= w || y >= h) return;
+    const float2 f = a.flow[(long long)y * w + x];
+    const int pitch = (int)(a.src.pitch_bytes / sizeof(Tv));
+    const Taps t = bilinear_taps(x, y, a.scale * f.x, a.scale * f.y, w, h, pitch, C);
+    const Tv* __restrict__ base = static_cast<const Tv*>(a.src.data);
+    float* out = reinterpret_cast<float*>(reinterpret_cast<char*>(a.dst) + (long long)y * a.dst_pitch_bytes) + x * C;
+    const float scale = sizeof(Tv) == 1 ? 1.0f / 255.0f : 1.0f;
+    for (int k = 0; k < C; ++k) out[k] = sample_channel(base, t, k) * scale;
+}
+
+}  // namespace
+
+cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
+    dim3 block(32, 8);
+    dim3 grid((a.L.w + 31) / 32, (a.L.h + 7) / 8);
+    if (a.L.dtype == 0) {
+        if (a.L.c == 3) blend_kernel<uint8_t, 3><<<grid, block, 0, s>>>(a);
+        else blend_kernel<uint8_t, 1><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.L.c == 3) blend_kernel<float, 3><<<grid, block, 0, s>>>(a);
+        else blend_kernel<float, 1><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp(const WarpArgs& a, cudaStream_t s) {
+    dim3 block(32, 8);
+    dim3 grid((a.src.w + 31) / 32, (a.src.h + 7) / 8);
+    if (a.src.dtype == 0) warp_kernel<uint8_t><<<grid, block, 0, s>>>(a);
+    else warp_kernel<float><<<grid, block, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace pano

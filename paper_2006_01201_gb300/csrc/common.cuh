@@ -1,0 +1,140 @@
+// common.cuh -- internal declarations shared by the kernels and the C ABI of
+// the optical-flow blend (Section III-C of the paper). Not a public header.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pano {
+
+constexpr int kMaxLevels = 12;
+
+// A float32 plane in device memory: rows of `pitch` elements.
+struct Plane {
+    const float* p;
+    int pitch;
+};
+
+// ---------------------------------------------------------------------------
+// Bilinear sample of a float plane at (qx + ox, qy + oy), pixel centres on
+// integer coordinates, each of the four taps clamped to [0, w-1] x [0, h-1].
+// The integer base (qx, qy) and the real offset (ox, oy) are kept apart so
+// that the fractional weights come from the offset alone: their rounding
+// error does not grow with the position in a large strip.
+// ---------------------------------------------------------------------------
+struct Taps {
+    int o00, o10, o01, o11;  // element offsets of the four taps
+    float ax, ay;            // weights of the second column / second row
+};
+
+__device__ __forceinline__ Taps bilinear_taps(int qx, int qy, float ox, float oy, int w, int h,
+                                              int pitch_elems, int elem_stride) {
+    // Beyond +-(size + 2) every tap clamps to the same edge pixel, so limiting
+    // the offset first changes no result and keeps the conversion defined.
+    ox = fminf(fmaxf(ox, -(float)(w + 2)), (float)(w + 2));
+    oy = fminf(fmaxf(oy, -(float)(h + 2)), (float)(h + 2));
+    float fx = floorf(ox), fy = floorf(oy);
+    Taps t;
+    t.ax = ox - fx;
+    t.ay = oy - fy;
+    int x0 = qx + (int)fx, y0 = qy + (int)fy;
+    int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
+    int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
+    t.o00 = ya * pitch_elems + xa * elem_stride;
+    t.o10 = ya * pitch_elems + xb * elem_stride;
+    t.o01 = yb * pitch_elems + xa * elem_stride;
+    t.o11 = yb * pitch_elems + xb * elem_stride;
+    return t;
+}
+
+__device__ __forceinline__ float bilinear_mix(const Taps& t, float i00, float i10, float i01,
+                                              float i11) {
+    float top = fmaf(t.ax, i10 - i00, i00);
+    float bot = fmaf(t.ax, i11 - i01, i01);
+    return fmaf(t.ay, bot - top, top);
+}
+
+__device__ __forceinline__ float sample_plane(const float* __restrict__ img, int pitch, int w, int h,
+                                              int qx, int qy, float ox, float oy) {
+    Taps t = bilinear_taps(qx, qy, ox, oy, w, h, pitch, 1);
+    return bilinear_mix(t, __ldg(img + t.o00), __ldg(img + t.o10), __ldg(img + t.o01),
+                        __ldg(img + t.o11));
+}
+
+// ---------------------------------------------------------------------------
+// Launch descriptors (host fills, kernels read by value).
+// ---------------------------------------------------------------------------
+struct ImageDesc {
+    const void* data;
+    int h, w, c;
+    long long pitch_bytes;
+    int dtype;  // 0 = u8, 1 = f32
+};
+
+// Level-0 luma of up to two images in one launch (blockIdx.z selects one).
+struct LumaArgs {
+    ImageDesc in[2];
+    float* out[2];
+    int out_pitch[2];
+    int count;
+};
+
+// One REDUCE step of up to two planes in one launch.
+struct PyrDownArgs {
+    const float* src[2];
+    float* dst[2];
+    int src_pitch[2], dst_pitch[2];
+    int h, w;  // source size
+    int count;
+};
+
+// One pyramid level of Lucas-Kanade in up to two directions (blockIdx.z).
+struct LkDir {
+    const float* T;   // template level
+    const float* J;   // target level
+    const float* uin; // starting / coarse flow (float2 elements), may be null
+    float* uout;      // result (float2 elements)
+    int pitchT, pitchJ;  // in floats
+    int uin_pitch;    // in float2 elements
+    int uout_pitch;   // in float2 elements
+};
+
+struct LkArgs {
+    LkDir dir[2];
+    int h, w;            // level size
+    int in_h, in_w;      // size of uin
+    int mode;            // 0 zero start, 1 upsample coarse uin, 2 uin as is
+    int iters, radius;
+    float lambda;
+    int tile_w, tile_h;
+};
+
+// Code 1 blend or the plain flow warp.
+struct BlendArgs {
+    ImageDesc L, R;
+    const float2* flowLR;
+    const float2* flowRL;
+    const float* blend;  // (h, w) or null -> Eq. (1) strip ramp
+    void* F;
+    long long F_pitch_bytes;
+    float k_sharp, k_mag;
+};
+
+struct WarpArgs {
+    ImageDesc src;
+    const float2* flow;
+    float scale;
+    float* dst;
+    long long dst_pitch_bytes;
+};
+
+// Launchers: enqueue on `s`, return the launch error (cudaSuccess if none).
+cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s);
+cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s);
+cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s);
+size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius);
+cudaError_t lk_prepare(int max_smem_bytes);
+cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
+cudaError_t launch_warp(const WarpArgs& a, cudaStream_t s);
+
+}  // namespace pano

@@ -1,0 +1,230 @@
+// lk.cu -- one pyramid level of dense Lucas-Kanade flow (Section III-C-1,
+// "LK pyramid algorithm"; the local least-squares flow of [20]).
+//
+// Every pixel p solves for a flow v that is constant over the (2r+1)^2 box
+// W(p); each box sample q is linearised at its own current flow u(q):
+//   (G(p) + lambda I) v = sum_{q in W(p)} grad T(q) (grad T(q) . u(q) - It(q)) + lambda u(p)
+//   It(q) = J(q + u(q)) - T(q),   G(p) = sum_{q in W(p)} grad T(q) grad T(q)^T
+// with the box clipped to the image, central-difference gradients of T and
+// bilinear clamp-to-edge sampling of J; then u(p) <- v. K such steps run per
+// level, starting from twice the bilinearly upsampled flow of the coarser
+// level (or zero at the coarsest level).
+//
+// GPU design: one CTA owns an output tile and iterates all K steps of the
+// level on chip. Because step k at p reads the flows of step k-1 on W(p),
+// the tile carries a halo of K*r pixels that shrinks by r per step; the
+// template, its gradient, the flow and the inverse normal matrices stay in
+// shared memory for the whole level, and only J is gathered from L1/L2. Each
+// step is: per-sample residual products -> column box sums -> row box sums
+// and the 2x2 solve. Both flow directions run in the same launch
+// (blockIdx.z). To keep FP32 rounding independent of the size of the flow,
+// the kernel works with flows relative to one reference flow per tile (the
+// starting flow at the tile centre); the equations above are unchanged by
+// that shift.
+#include "common.cuh"
+
+namespace pano {
+
+namespace {
+
+constexpr int kLkThreads = 512;
+
+__device__ __forceinline__ float2 start_flow(const LkArgs& a, const LkDir& D, int x, int y) {
+    if (a.mode == 0 || D.uin == nullptr) return make_float2(0.f, 0.f);
+    const float2* __restrict__ u = reinterpret_cast<const float2*>(D.uin);
+    if (a.mode == 2) return u[(long long)y * D.uin_pitch + x];
+    // coarse-to-fine: 2 * bilinear(u_coarse)(x/2, y/2); fine pixel 2i sits on
+    // coarse pixel i, so the weights are 0 or 1/2
+    int x0 = x >> 1, y0 = y >> 1;
+    float fx = (x & 1) ? 0.5f : 0.f, fy = (y & 1) ? 0.5f : 0.f;
+    int xa = min(x0, a.in_w - 1), xb = min(x0 + 1, a.in_w - 1);
+    int ya = min(y0, a.in_h - 1), yb = min(y0 + 1, a.in_h - 1);
+    float2 u00 = u[(long long)ya * D.uin_pitch + xa], u10 = u[(long long)ya * D.uin_pitch + xb];
+    float2 u01 = u[(long long)yb * D.uin_pitch + xa], u11 = u[(long long)yb * D.uin_pitch + xb];
+    float tx = fmaf(fx, u10.x - u00.x, u00.x), bx = fmaf(fx, u11.x - u01.x, u01.x);
+    float ty = fmaf(fx, u10.y - u00.y, u00.y), by = fmaf(fx, u11.y - u01.y, u01.y);
+    return make_float2(2.f * fmaf(fy, bx - tx, tx), 2.f * fmaf(fy, by - ty, ty));
+}
+
+template <int RAD>
+__global__ void __launch_bounds__(kLkThreads) lk_level_kernel(LkArgs a) {
+    extern __shared__ float4 smem4[];
+    const LkDir D = a.dir[blockIdx.z];
+    const int K = a.iters;
+    const int halo = K * RAD;
+    const int RW = a.tile_w + 2 * halo, RH = a.tile_h + 2 * halo;
+    const int N = RW * RH;
+    float4* sGi = smem4;                                  // inverse normal matrix (i11, i12, i22)
+    float2* sG = reinterpret_cast<float2*>(sGi + N);      // grad T
+    float2* sU = sG + N;                                  // flow relative to the reference
+    float2* sP = sU + N;                                  // per-sample products
+    float2* sV = sP + N;                                  // column box sums
+    float* sT = reinterpret_cast<float*>(sV + N);         // template
+    const int ox = blockIdx.x * a.tile_w - halo, oy = blockIdx.y * a.tile_h - halo;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int w = a.w, h = a.h, pitchT = D.pitchT, pitchJ = D.pitchJ;
+    const float* __restrict__ T = D.T;
+    const float* __restrict__ J = D.J;
+
+    // Phase 0: template, its gradient and the starting flow on the region.
+    for (int ry = warp; ry < RH; ry += nwarps) {
+        const int y = oy + ry;
+        for (int rx = lane; rx < RW; rx += 32) {
+            const int x = ox + rx;
+            float t = 0.f;
+            float2 g = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f);
+            if (x >= 0 && x < w && y >= 0 && y < h) {
+                const float* row = T + (long long)y * pitchT;
+                t = __ldg(row + x);
+                g.x = 0.5f * (__ldg(row + min(x + 1, w - 1)) - __ldg(row + max(x - 1, 0)));
+                g.y = 0.5f * (__ldg(T + (long long)min(y + 1, h - 1) * pitchT + x) -
+                              __ldg(T + (long long)max(y - 1, 0) * pitchT + x));
+                u = start_flow(a, D, x, y);
+            }
+            const int i = ry * RW + rx;
+            sT[i] = t;
+            sG[i] = g;
+            sU[i] = u;
+        }
+    }
+    __syncthreads();
+
+    // Reference flow: the starting flow at the tile centre (inside the image).
+    const int cx = min(blockIdx.x * a.tile_w + a.tile_w / 2, w - 1);
+    const int cy = min(blockIdx.y * a.tile_h + a.tile_h / 2, h - 1);
+    const float2 ref = sU[(cy - oy) * RW + (cx - ox)];
+
+    if (K > 0) {
+        __syncthreads();  // everyone has read ref before it is overwritten
+        // Relative flows and the inverse normal matrices on R_1 (margin RAD).
+        for (int ry = warp; ry < RH; ry += nwarps) {
+            for (int rx = lane; rx < RW; rx += 32) {
+                const int i = ry * RW + rx;
+                float2 u = sU[i];
+                sU[i] = make_float2(u.x - ref.x, u.y - ref.y);
+                if (ry < RAD || ry >= RH - RAD || rx < RAD || rx >= RW - RAD) continue;
+                float g11 = 0.f, g12 = 0.f, g22 = 0.f;
+#pragma unroll
+                for (int dy = -RAD; dy <= RAD; ++dy)
+#pragma unroll
+                    for (int dx = -RAD; dx <= RAD; ++dx) {
+                        float2 g = sG[i + dy * RW + dx];
+                        g11 = fmaf(g.x, g.x, g11);
+                        g12 = fmaf(g.x, g.y, g12);
+                        g22 = fmaf(g.y, g.y, g22);
+                    }
+                const float a11 = g11 + a.lambda, a22 = g22 + a.lambda;
+                const float inv = 1.0f / (a11 * a22 - g12 * g12);
+                sGi[i] = make_float4(a22 * inv, -g12 * inv, a11 * inv, 0.f);
+            }
+        }
+        __syncthreads();
+
+        for (int k = 1; k <= K; ++k) {
+            const int mA = (k - 1) * RAD, mC = k * RAD;
+            // A: products grad T(q) * s(q), s = grad T . u(q) - It(q), on R_{k-1}
+            for (int ry = mA + warp; ry < RH - mA; ry += nwarps) {
+                const int y = oy + ry;
+                for (int rx = mA + lane; rx < RW - mA; rx += 32) {
+                    const int x = ox + rx;
+                    const int i = ry * RW + rx;
+                    float2 P = make_float2(0.f, 0.f);
+                    if (x >= 0 && x < w && y >= 0 && y < h) {
+                        const float2 u = sU[i];
+                        const float2 g = sG[i];
+                        const float Jw = sample_plane(J, pitchJ, w, h, x, y, ref.x + u.x, ref.y + u.y);
+                        const float It = Jw - sT[i];
+                        const float s = fmaf(g.x, u.x, fmaf(g.y, u.y, -It));
+                        P = make_float2(g.x * s, g.y * s);
+                    }
+                    sP[i] = P;
+                }
+            }
+            __syncthreads();
+            // B: sums over the column window, rows of R_k, columns of R_{k-1}
+            for (int ry = mC + warp; ry < RH - mC; ry += nwarps) {
+                for (int rx = mA + lane; rx < RW - mA; rx += 32) {
+                    const int i = ry * RW + rx;
+                    float2 v = sP[i - RAD * RW];
+#pragma unroll
+                    for (int dy = -RAD + 1; dy <= RAD; ++dy) {
+                        float2 q = sP[i + dy * RW];
+                        v.x += q.x;
+                        v.y += q.y;
+                    }
+                    sV[i] = v;
+                }
+            }
+            __syncthreads();
+            // C: sums over the row window and the 2x2 solve on R_k
+            for (int ry = mC + warp; ry < RH - mC; ry += nwarps) {
+                const int y = oy + ry;
+                for (int rx = mC + lane; rx < RW - mC; rx += 32) {
+                    const int x = ox + rx;
+                    if (x < 0 || x >= w || y < 0 || y >= h) continue;
+                    const int i = ry * RW + rx;
+                    float2 m = sV[i - RAD];
+#pragma unroll
+                    for (int dx = -RAD + 1; dx <= RAD; ++dx) {
+                        float2 q = sV[i + dx];
+                        m.x += q.x;
+                        m.y += q.y;
+                    }
+                    const float2 u = sU[i];
+                    const float4 gi = sGi[i];
+                    const float r1 = fmaf(a.lambda, u.x, m.x), r2 = fmaf(a.lambda, u.y, m.y);
+                    sU[i] = make_float2(fmaf(gi.x, r1, gi.y * r2), fmaf(gi.y, r1, gi.z * r2));
+                }
+            }
+            __syncthreads();
+        }
+    }
+
+    // Write the tile (relative flows back to absolute).
+    const float2 add = (K > 0) ? ref : make_float2(0.f, 0.f);
+    float2* __restrict__ uo = reinterpret_cast<float2*>(D.uout);
+    for (int ty = warp; ty < a.tile_h; ty += nwarps) {
+        const int y = blockIdx.y * a.tile_h + ty;
+        if (y >= h) break;
+        for (int tx = lane; tx < a.tile_w; tx += 32) {
+            const int x = blockIdx.x * a.tile_w + tx;
+            if (x >= w) break;
+            const float2 u = sU[(ty + halo) * RW + (tx + halo)];
+            uo[(long long)y * D.uout_pitch + x] = make_float2(u.x + add.x, u.y + add.y);
+        }
+    }
+}
+
+template <int RAD>
+cudaError_t launch_rad(const LkArgs& a, int ndirs, cudaStream_t s) {
+    size_t smem = lk_smem_bytes(a.tile_w, a.tile_h, a.iters, a.radius);
+    dim3 grid((a.w + a.tile_w - 1) / a.tile_w, (a.h + a.tile_h - 1) / a.tile_h, ndirs);
+    lk_level_kernel<RAD><<<grid, kLkThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius) {
+    size_t halo = (size_t)iters * radius;
+    size_t n = (tile_w + 2 * halo) * (tile_h + 2 * halo);
+    return n * (sizeof(float4) + 4 * sizeof(float2) + sizeof(float));
+}
+
+cudaError_t lk_prepare(int max_smem_bytes) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(lk_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(lk_level_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes)) != cudaSuccess) return e;
+    return cudaFuncSetAttribute(lk_level_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
+}
+
+cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s) {
+    switch (a.radius) {
+        case 1: return launch_rad<1>(a, ndirs, s);
+        case 2: return launch_rad<2>(a, ndirs, s);
+        case 3: return launch_rad<3>(a, ndirs, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace pano

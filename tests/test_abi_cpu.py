@@ -1,0 +1,105 @@
+"""The C ABI on a machine without a GPU: the library loads, exports every
+function the header declares, and rejects bad arguments on the host before
+touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2006_01201_gb300 import binding, build
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pano_flow.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return binding.load_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    return re.findall(r"^PANO_API\s+[\w\s\*]+?\b(pano_\w+)\s*\(", src, flags=re.M)
+
+
+def test_header_declares_the_boundary():
+    names = set(declared_functions())
+    assert {"pano_flow_create", "pano_flow_pair", "pano_blend_pair", "pano_flow_destroy"} <= names
+    assert names == set(binding.SIGNATURES), "binding and header disagree"
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_params_default(lib):
+    p = binding.PanoParams()
+    lib.pano_flow_params_default(ctypes.byref(p))
+    assert (p.levels, p.iters, p.radius) == (4, 5, 2)
+    assert abs(p.lam - 1e-2) < 1e-9 and p.soft_sharpness == 10.0 and p.flow_mag_coef == 20.0
+    assert p.pyr_dtype == binding.PANO_F32
+
+
+def test_create_rejects_bad_arguments_before_any_device_call(lib):
+    out = ctypes.c_void_p(123)
+    p = binding.PanoParams()
+    lib.pano_flow_params_default(ctypes.byref(p))
+    assert lib.pano_flow_create(None, 10, 10, 1, ctypes.byref(out)) == binding.PANO_ERR_INVALID_ARG
+    assert out.value is None
+    assert b"params" in lib.pano_last_error(None)
+    assert lib.pano_flow_create(ctypes.byref(p), 10, 10, 1, None) == binding.PANO_ERR_INVALID_ARG
+    for field, value in (("levels", 0), ("levels", 13), ("iters", -1), ("iters", 17), ("radius", 0),
+                         ("radius", 4), ("lam", -1.0), ("lam", float("nan"))):
+        q = binding.PanoParams()
+        lib.pano_flow_params_default(ctypes.byref(q))
+        setattr(q, field, value)
+        assert lib.pano_flow_create(ctypes.byref(q), 10, 10, 1, ctypes.byref(out)) == \
+            binding.PANO_ERR_INVALID_ARG, (field, value)
+    q = binding.PanoParams()
+    lib.pano_flow_params_default(ctypes.byref(q))
+    q.pyr_dtype = binding.PANO_BF16
+    assert lib.pano_flow_create(ctypes.byref(q), 10, 10, 1, ctypes.byref(out)) == binding.PANO_ERR_UNSUPPORTED
+    assert lib.pano_flow_create(ctypes.byref(p), 0, 10, 1, ctypes.byref(out)) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_flow_create(ctypes.byref(p), 10, 10, 2, ctypes.byref(out)) == binding.PANO_ERR_INVALID_ARG
+
+
+def test_calls_reject_null_and_bad_images(lib):
+    assert lib.pano_flow_destroy(None) == binding.PANO_OK
+    img = binding.PanoImage(0x1000, 8, 8, 1, 32, binding.PANO_F32)
+    assert lib.pano_flow_pair(None, ctypes.byref(img), ctypes.byref(img), 0x2000, 0x3000, None) == \
+        binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_blend_pair(None, ctypes.byref(img), ctypes.byref(img), 0x2000, 0x3000, None,
+                               ctypes.byref(img), None) == binding.PANO_ERR_INVALID_ARG
+    # stage calls validate on the host too
+    bad = [
+        binding.PanoImage(None, 8, 8, 1, 32, binding.PANO_F32),         # null data
+        binding.PanoImage(0x1000, 0, 8, 1, 32, binding.PANO_F32),       # empty
+        binding.PanoImage(0x1000, 8, 8, 1, 16, binding.PANO_F32),       # pitch < row
+        binding.PanoImage(0x1002, 8, 8, 1, 32, binding.PANO_F32),       # misaligned
+        binding.PanoImage(0x1000, 8, 8, 1, 34, binding.PANO_F32),       # pitch not a multiple
+        binding.PanoImage(0x1000, 8, 8, 7, 64, binding.PANO_U8),        # channels
+        binding.PanoImage(0x1000, 8, 8, 1, 32, 9),                      # dtype
+    ]
+    expect = [1, 1, 1, 1, 1, 2, 1]
+    for im, st in zip(bad, expect):
+        assert lib.pano_stage_luma(ctypes.byref(im), 0x2000, 8, None) == st
+    half = binding.PanoImage(0x1000, 8, 8, 1, 16, binding.PANO_BF16)
+    assert lib.pano_stage_luma(ctypes.byref(half), 0x2000, 8, None) == binding.PANO_ERR_UNSUPPORTED
+    assert lib.pano_stage_pyr_down(None, 8, 8, 8, 0x2000, 4, None) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_stage_pyr_down(0x1000, 8, 8, 7, 0x2000, 4, None) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_stage_lk(0x1000, 0x2000, 8, 8, 8, None, 0, 0, 0, 0x3004, 5, 2, 0.01, None) == \
+        binding.PANO_ERR_INVALID_ARG   # flow_out not 8-byte aligned
+    assert lib.pano_stage_lk(0x1000, 0x2000, 8, 8, 8, None, 0, 0, 0, 0x3000, 5, 9, 0.01, None) == \
+        binding.PANO_ERR_INVALID_ARG   # radius
+    assert lib.pano_stage_lk(0x1000, 0x2000, 8, 8, 8, 0x3000, 8, 8, 0, 0x3100, 1, 2, 0.01, None) == \
+        binding.PANO_ERR_INVALID_ARG   # flow_in overlaps flow_out
+    assert b"overlap" in lib.pano_last_error(None)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setattr(binding, "_lib", None)
+    with pytest.raises(binding.PanoError):
+        binding.load_library(str(tmp_path / "nope.so"))
