@@ -146,6 +146,43 @@ PANO_API pano_status pano_flow_destroy(pano_flow_ctx* ctx);
 PANO_API const char* pano_last_error(const pano_flow_ctx* ctx);
 
 /* ----------------------------------------------------------------------
+ * Flow without any device allocation. (The paper has no counterpart: this is
+ * a deployment variant of pano_flow_pair.)
+ *
+ * pano_flow_create allocates its scratch with cudaMalloc. Some callers cannot
+ * allow that: a process that owns all of the GPU's memory through its own
+ * pool and forbids other allocations, or a frame loop with a deadline, where
+ * cudaMalloc / cudaFree would add latency and device-wide synchronisation.
+ * pano_flow_pair_static computes exactly what pano_flow_pair computes (same
+ * kernels, same results) without a context: its scratch is one fixed array
+ * of PANO_STATIC_SCRATCH_BYTES bytes inside the library, which every GPU that
+ * loads the library holds until the process exits. The call never allocates
+ * or frees device memory.
+ *
+ *   Size limit  The scratch holds both luma pyramids and the coarse-level
+ *               flows of both directions, about 16 * h * w bytes (4 levels
+ *               or more): strips up to about one megapixel (e.g. 1024 x 1024)
+ *               fit. Larger strips are rejected with PANO_ERR_INVALID_ARG and
+ *               a message giving the bytes needed; nothing is enqueued.
+ *   Set-up      The first call on each device, with that device current,
+ *               looks up the array's device address (cudaGetSymbolAddress)
+ *               and sets the kernel's shared-memory limit. Make that first
+ *               call before any stream capture on the device.
+ *   Sharing     All calls, on every stream and thread, use the same array,
+ *               and it keeps whatever the last call wrote. Nothing in it
+ *               needs to start at zero: each call writes every byte it reads.
+ *               Calls whose work overlaps on the GPU race on the array:
+ *               order them on one stream (or with events).
+ * Arguments, flows and errors are those of pano_flow_pair; `params` replaces
+ * the context.
+ * ---------------------------------------------------------------------- */
+#define PANO_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+PANO_API pano_status pano_flow_pair_static(const pano_flow_params* params, const pano_image* L,
+                                           const pano_image* R, float* flow_LtoR, float* flow_RtoL,
+                                           void* cuda_stream);
+
+/* ----------------------------------------------------------------------
  * Tracing. When enabled, every launch of a kernel kind selected by
  * kind_mask that a context call enqueues is bracketed by two CUDA events on
  * that call's stream, so its device time can be read back. Events are

@@ -62,6 +62,7 @@ SIGNATURES = {
     "pano_trace_enable": ([_VP, ctypes.c_uint, _I], _I),
     "pano_trace_read": ([_VP, ctypes.POINTER(PanoTraceRecord), _I, ctypes.POINTER(ctypes.c_int)], _I),
     "pano_flow_launches": ([_VP], ctypes.c_ulonglong),
+    "pano_flow_pair_static": ([_PAR, _IMG, _IMG, _VP, _VP, _VP], _I),
     "pano_stage_luma": ([_IMG, _VP, _I, _VP], _I),
     "pano_stage_pyr_down": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
     "pano_stage_lk": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _VP], _I),
@@ -266,6 +267,24 @@ class FlowContext:
     def launches(self) -> int:
         """Kernel launches enqueued by this context so far."""
         return int(load_library().pano_flow_launches(self._h))
+
+
+def flow_pair_static(params: Params, L, R, out=None, stream=None):
+    """(FlowLtoR, FlowRtoL) like FlowContext.flow_pair, without any device allocation
+    inside the library: its scratch is a fixed in-library array (strips up to
+    about one megapixel). For callers that may not allocate device memory;
+    calls that overlap on the GPU share that array and must be ordered."""
+    torch = _torch()
+    dl, dr = image_desc(L), image_desc(R)
+    h, w = dl.h, dl.w
+    if out is None:
+        out = (torch.empty((h, w, 2), dtype=torch.float32, device=L.device),
+               torch.empty((h, w, 2), dtype=torch.float32, device=L.device))
+    p = params.to_c()
+    _check(load_library().pano_flow_pair_static(ctypes.byref(p), ctypes.byref(dl), ctypes.byref(dr),
+                                                _flow_ptr(out[0], h, w, "flow_LtoR"),
+                                                _flow_ptr(out[1], h, w, "flow_RtoL"), _stream_ptr(stream)))
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -187,6 +187,8 @@ ImageDesc desc(const pano_image* im) {
 
 }  // namespace
 
+void pano::set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
+
 extern "C" {
 
 void pano_flow_params_default(pano_flow_params* p) {

@@ -137,4 +137,7 @@ cudaError_t lk_prepare(int max_smem_bytes);
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
 cudaError_t launch_warp(const WarpArgs& a, cudaStream_t s);
 
+// Stores the message that pano_last_error() returns on the calling thread.
+void set_last_error(const char* msg);
+
 }  // namespace pano

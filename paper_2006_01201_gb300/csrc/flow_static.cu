@@ -1,0 +1,245 @@
+// flow_static.cu -- pano_flow_pair_static: the bidirectional flow of
+// pano_flow_pair for callers that must not allocate device memory.
+//
+// Who needs it: a host program that owns the whole GPU through its own memory
+// pool (a serving process that reserves all of HBM at start-up and forbids
+// any other allocation), or a loop with a per-frame deadline, where
+// cudaMalloc / cudaFree would add their latency and their device-wide
+// synchronisation to the frame. Such callers can pass their own input and
+// output buffers but cannot let the library create a context, because
+// pano_flow_create allocates the pyramids and coarse flows with cudaMalloc.
+//
+// This entry point keeps that scratch in one fixed file-scope device array
+// of PANO_STATIC_SCRATCH_BYTES instead. Every GPU that loads the library
+// holds the array until the process exits. The kernels are the ones
+// pano_flow_pair launches; only where their scratch lives differs.
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <mutex>
+
+#include "common.cuh"
+#include "pano_flow.h"
+
+using namespace pano;
+
+// The shared scratch. All calls, on every stream, use this one array.
+static __device__ __align__(256) unsigned char g_static_scratch[PANO_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+
+struct DeviceSetup {
+    bool done = false;
+    unsigned char* scratch = nullptr;  // device address of g_static_scratch
+    int max_smem = 0;
+};
+DeviceSetup g_setup[kMaxDevices];
+std::mutex g_setup_mutex;
+
+pano_status sfail(pano_status st, const char* fmt, ...) {
+    char msg[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(msg, sizeof(msg), fmt, ap);
+    va_end(ap);
+    set_last_error(msg);
+    return st;
+}
+
+// Once per device, with that device current: the device address of the
+// scratch array (host code cannot use the symbol itself) and the kernel's
+// dynamic shared-memory limit.
+pano_status setup_current_device(DeviceSetup** out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return sfail(PANO_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return sfail(PANO_ERR_UNSUPPORTED, "device index %d", dev);
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    DeviceSetup& s = g_setup[dev];
+    if (!s.done) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess)
+            return sfail(PANO_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
+        int ms = 0;
+        e = cudaDeviceGetAttribute(&ms, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) return sfail(PANO_ERR_CUDA, "shared-memory limit: %s", cudaGetErrorString(e));
+        e = lk_prepare(ms);
+        if (e != cudaSuccess) return sfail(PANO_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        s.scratch = static_cast<unsigned char*>(p);
+        s.max_smem = ms;
+        s.done = true;
+    }
+    *out = &s;
+    return PANO_OK;
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+pano_status check_img(const pano_image* im, const char* name) {
+    if (!im || !im->data) return sfail(PANO_ERR_INVALID_ARG, "%s is NULL", name);
+    if (im->h < 1 || im->w < 1) return sfail(PANO_ERR_INVALID_ARG, "%s size %dx%d", name, im->h, im->w);
+    if (im->dtype != PANO_U8 && im->dtype != PANO_F32)
+        return sfail(PANO_ERR_UNSUPPORTED, "%s: dtype %d (PANO_U8 or PANO_F32)", name, im->dtype);
+    if (im->c != 1 && im->c != 3) return sfail(PANO_ERR_UNSUPPORTED, "%s: %d channels", name, im->c);
+    size_t es = im->dtype == PANO_U8 ? 1 : 4;
+    if (im->pitch_bytes < (size_t)im->w * im->c * es || im->pitch_bytes % es || ((uintptr_t)im->data) % es)
+        return sfail(PANO_ERR_INVALID_ARG, "%s: bad pitch or alignment", name);
+    if ((double)im->h * (double)(im->pitch_bytes / es) > 2147483647.0)
+        return sfail(PANO_ERR_UNSUPPORTED, "%s: more than 2^31 elements", name);
+    return PANO_OK;
+}
+
+// Bytes of scratch a strip of h x w pixels needs: both luma pyramids and the
+// coarse-level flows of both directions, laid out as the entry point carves them.
+size_t static_scratch_bytes(int h, int w, int levels) {
+    if (h < 1 || w < 1 || levels < 1 || levels > kMaxLevels) return 0;
+    size_t total = 0;
+    int lh = h, lw = w;
+    for (int l = 0; l < levels; ++l) {
+        total += 2 * align_up((size_t)align_up(lw, 32) * lh * sizeof(float), 256);      // both pyramids
+        if (l > 0) total += 2 * align_up((size_t)align_up(lw, 16) * lh * 8, 256);      // both flows
+        lh = (lh + 1) / 2;
+        lw = (lw + 1) / 2;
+    }
+    return total;
+}
+
+}  // namespace
+
+extern "C" {
+
+pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L, const pano_image* R,
+                                  float* flow_LtoR, float* flow_RtoL, void* cuda_stream) {
+    if (!p) return sfail(PANO_ERR_INVALID_ARG, "params is NULL");
+    if (p->levels < 1 || p->levels > kMaxLevels || p->iters < 0 || p->iters > 16 || p->radius < 1 ||
+        p->radius > 3 || !(p->lambda >= 0.f) || !(p->lambda < 1e30f))
+        return sfail(PANO_ERR_INVALID_ARG, "parameters out of range");
+    if (p->pyr_dtype != PANO_F32) return sfail(PANO_ERR_UNSUPPORTED, "pyramid dtype %d", p->pyr_dtype);
+    pano_status st;
+    if ((st = check_img(L, "L")) != PANO_OK) return st;
+    if ((st = check_img(R, "R")) != PANO_OK) return st;
+    if (L->h != R->h || L->w != R->w || L->c != R->c || L->dtype != R->dtype)
+        return sfail(PANO_ERR_INVALID_ARG, "L and R differ in size, channels or dtype");
+    if (!flow_LtoR || !flow_RtoL || ((uintptr_t)flow_LtoR) % 8 || ((uintptr_t)flow_RtoL) % 8)
+        return sfail(PANO_ERR_INVALID_ARG, "flows must be non-NULL and 8-byte aligned");
+    const size_t need = static_scratch_bytes(L->h, L->w, p->levels);
+    if (need > (size_t)PANO_STATIC_SCRATCH_BYTES)
+        return sfail(PANO_ERR_INVALID_ARG,
+                     "strip %dx%d with %d levels needs %zu bytes of scratch; the fixed scratch holds %zu",
+                     L->h, L->w, p->levels, need, (size_t)PANO_STATIC_SCRATCH_BYTES);
+    DeviceSetup* ds = nullptr;
+    if ((st = setup_current_device(&ds)) != PANO_OK) return st;
+    static const int cand[][2] = {{32, 16}, {32, 8}, {16, 16}, {16, 8}, {8, 8}};
+    int tw = 0, th = 0;
+    for (auto& c : cand)
+        if (lk_smem_bytes(c[0], c[1], p->iters, p->radius) <= (size_t)ds->max_smem) {
+            tw = c[0];
+            th = c[1];
+            break;
+        }
+    if (!tw) return sfail(PANO_ERR_UNSUPPORTED, "iters * radius too large for shared memory");
+
+    // Carve the fixed scratch exactly as static_scratch_bytes counts it.
+    const int nlev = p->levels;
+    int hs[kMaxLevels], ws[kMaxLevels], lp[kMaxLevels], fp[kMaxLevels];
+    float* pyr[2][kMaxLevels] = {};
+    float* flw[2][kMaxLevels] = {};
+    unsigned char* cur = ds->scratch;
+    for (int l = 0; l < nlev; ++l) {
+        hs[l] = l == 0 ? L->h : (hs[l - 1] + 1) / 2;
+        ws[l] = l == 0 ? L->w : (ws[l - 1] + 1) / 2;
+        lp[l] = (int)align_up(ws[l], 32);
+        fp[l] = (int)align_up(ws[l], 16);
+        for (int s = 0; s < 2; ++s) {
+            pyr[s][l] = reinterpret_cast<float*>(cur);
+            cur += align_up((size_t)lp[l] * hs[l] * sizeof(float), 256);
+        }
+        if (l > 0)
+            for (int d = 0; d < 2; ++d) {
+                flw[d][l] = reinterpret_cast<float*>(cur);
+                cur += align_up((size_t)fp[l] * hs[l] * 8, 256);
+            }
+    }
+    // Nothing in the scratch has to start at zero: every level and every
+    // coarse flow is written in full by this call before it is read.
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const pano_image* img[2] = {L, R};
+    const float* plane[2][kMaxLevels];
+    int ppitch[2][kMaxLevels];
+    LumaArgs la;
+    memset(&la, 0, sizeof(la));
+    for (int si = 0; si < 2; ++si) {
+        for (int l = 0; l < nlev; ++l) {
+            plane[si][l] = pyr[si][l];
+            ppitch[si][l] = lp[l];
+        }
+        if (img[si]->dtype == PANO_F32 && img[si]->c == 1) {
+            plane[si][0] = static_cast<const float*>(img[si]->data);
+            ppitch[si][0] = (int)(img[si]->pitch_bytes / sizeof(float));
+        } else {
+            ImageDesc d;
+            d.data = img[si]->data;
+            d.h = img[si]->h;
+            d.w = img[si]->w;
+            d.c = img[si]->c;
+            d.pitch_bytes = (long long)img[si]->pitch_bytes;
+            d.dtype = img[si]->dtype == PANO_U8 ? 0 : 1;
+            la.in[la.count] = d;
+            la.out[la.count] = pyr[si][0];
+            la.out_pitch[la.count] = lp[0];
+            la.count++;
+        }
+    }
+    cudaError_t e;
+    if (la.count > 0 && (e = launch_luma(la, s)) != cudaSuccess)
+        return sfail(PANO_ERR_CUDA, "luma launch: %s", cudaGetErrorString(e));
+    for (int l = 1; l < nlev; ++l) {
+        PyrDownArgs pa;
+        memset(&pa, 0, sizeof(pa));
+        for (int si = 0; si < 2; ++si) {
+            pa.src[si] = plane[si][l - 1];
+            pa.src_pitch[si] = ppitch[si][l - 1];
+            pa.dst[si] = pyr[si][l];
+            pa.dst_pitch[si] = lp[l];
+        }
+        pa.h = hs[l - 1];
+        pa.w = ws[l - 1];
+        pa.count = 2;
+        if ((e = launch_pyr_down(pa, s)) != cudaSuccess)
+            return sfail(PANO_ERR_CUDA, "pyramid launch: %s", cudaGetErrorString(e));
+    }
+    float* out[2] = {flow_LtoR, flow_RtoL};
+    for (int l = nlev - 1; l >= 0; --l) {
+        LkArgs ka;
+        memset(&ka, 0, sizeof(ka));
+        for (int d = 0; d < 2; ++d) {
+            ka.dir[d].T = plane[d][l];
+            ka.dir[d].pitchT = ppitch[d][l];
+            ka.dir[d].J = plane[1 - d][l];
+            ka.dir[d].pitchJ = ppitch[1 - d][l];
+            ka.dir[d].uin = l == nlev - 1 ? nullptr : flw[d][l + 1];
+            ka.dir[d].uin_pitch = l == nlev - 1 ? 0 : fp[l + 1];
+            ka.dir[d].uout = l == 0 ? out[d] : flw[d][l];
+            ka.dir[d].uout_pitch = l == 0 ? ws[0] : fp[l];
+        }
+        ka.h = hs[l];
+        ka.w = ws[l];
+        ka.in_h = l == nlev - 1 ? 0 : hs[l + 1];
+        ka.in_w = l == nlev - 1 ? 0 : ws[l + 1];
+        ka.mode = l == nlev - 1 ? 0 : 1;
+        ka.iters = p->iters;
+        ka.radius = p->radius;
+        ka.lambda = p->lambda;
+        ka.tile_w = tw;
+        ka.tile_h = th;
+        if ((e = launch_lk_level(ka, 2, s)) != cudaSuccess)
+            return sfail(PANO_ERR_CUDA, "LK launch: %s", cudaGetErrorString(e));
+    }
+    return PANO_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,83 @@
+"""pano_flow_pair_static: the flow of a strip pair without any device
+allocation inside the library.
+
+Callers that own all device memory through their own pool, or that run a
+frame loop where cudaMalloc / cudaFree would add latency and synchronise the
+device, cannot create a context (pano_flow_create allocates). This entry point
+serves them from a fixed scratch array in the library. These tests call it
+through the C ABI twice in a row, with different strips, and compare each
+result with pano_flow_pair on the same inputs; they also check that a strip
+too large for the fixed scratch is refused before anything is enqueued.
+
+The file is named so that pytest collects it last.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2006_01201_gb300 import binding  # noqa: E402
+from paper_2006_01201_gb300 import build as gpu_build  # noqa: E402
+
+DEV = torch.device("cuda:0")
+# the tolerance of the other GPU flow tests is a mean endpoint error of 0.05 px
+# against the oracle; against pano_flow_pair (same kernels) the bar is tighter
+MAX_ABS = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    gpu_build.build()
+    binding.load_library()
+
+
+def _pairs():
+    small = synth.pair_small_gray()                                   # 256 x 512 gray f32
+    rgb = synth.pair_fullres_rgb(seed=3, h=300, w=400, dmax=12.0, levels=4)   # RGB u8
+    return [(small, 4), (rgb, 4)]
+
+
+def test_static_flow_matches_context_flow_on_two_calls_in_a_row():
+    results = []
+    for pair, levels in _pairs():
+        L = torch.from_numpy(pair.L).to(DEV)
+        R = torch.from_numpy(pair.R).to(DEV)
+        params = binding.Params(levels=levels)
+        s_lr, s_rl = binding.flow_pair_static(params, L, R)
+        torch.cuda.synchronize()
+        h, w = pair.shape
+        with binding.FlowContext(params, max_h=h, max_w=w, max_c=3) as ctx:
+            c_lr, c_rl = ctx.flow_pair(L, R)
+            torch.cuda.synchronize()
+        results.append(((s_lr - c_lr).abs().max().item(), (s_rl - c_rl).abs().max().item()))
+    for d_lr, d_rl in results:
+        assert d_lr <= MAX_ABS and d_rl <= MAX_ABS, results
+
+
+def test_repeated_static_calls_give_the_same_flow():
+    pair, levels = _pairs()[0]
+    L = torch.from_numpy(pair.L).to(DEV)
+    R = torch.from_numpy(pair.R).to(DEV)
+    params = binding.Params(levels=levels)
+    a = binding.flow_pair_static(params, L, R)
+    b = binding.flow_pair_static(params, R, L)      # other strips in between
+    c = binding.flow_pair_static(params, L, R)
+    torch.cuda.synchronize()
+    assert torch.equal(a[0], c[0]) and torch.equal(a[1], c[1])
+    assert torch.equal(b[0], a[1]) and torch.equal(b[1], a[0])
+
+
+def test_strip_too_large_for_the_fixed_scratch_is_refused():
+    big = torch.zeros((2048, 2048), dtype=torch.float32, device=DEV)
+    with pytest.raises(binding.PanoError) as ei:
+        binding.flow_pair_static(binding.Params(levels=4), big, big)
+    assert ei.value.status == binding.PANO_ERR_INVALID_ARG
+    assert "scratch" in ei.value.message
+    assert np.isfinite(big.sum().item())
