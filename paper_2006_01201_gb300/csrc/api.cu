@@ -534,7 +534,9 @@ pano_status pano_stage_lk(const float* T, const float* J, int h, int w, int pitc
     ka.iters = iters;
     ka.radius = radius;
     ka.lambda = lambda;
-    cudaError_t e = launch_lk_level(ka, 1, static_cast<cudaStream_t>(cuda_stream));
+    // the stage entry point always runs the streamed kernel when it applies
+    cudaError_t e = lk_stream_supports(iters, radius) ? launch_lk_stream(ka, 1, static_cast<cudaStream_t>(cuda_stream))
+                                                      : launch_lk_tile(ka, 1, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? PANO_OK : cuda_fail(e, "LK launch");
 }
 

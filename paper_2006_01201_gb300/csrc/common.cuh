@@ -131,7 +131,15 @@ struct WarpArgs {
 // Launchers: enqueue on `s`, return the launch error (cudaSuccess if none).
 cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s);
 cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s);
+// One LK level: streamed (lk_stream.cu) for levels of at least
+// kStreamMinPixels pixels and 1 <= iters <= 5, tiled (lk.cu) otherwise.
+constexpr long long kStreamMinPixels = 100000;
 cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s);
+cudaError_t launch_lk_tile(const LkArgs& a, int ndirs, cudaStream_t s);
+// Streamed form of the same level (lk_stream.cu), used for 1 <= iters <= 5.
+bool lk_stream_supports(int iters, int radius);
+cudaError_t lk_stream_prepare(int max_smem_bytes);
+cudaError_t launch_lk_stream(const LkArgs& a, int ndirs, cudaStream_t s);
 size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius);
 cudaError_t lk_prepare(int max_smem_bytes);
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);

@@ -213,12 +213,21 @@ size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius) {
 
 cudaError_t lk_prepare(int max_smem_bytes) {
     cudaError_t e;
+    if ((e = lk_stream_prepare(max_smem_bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(lk_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes)) != cudaSuccess) return e;
     if ((e = cudaFuncSetAttribute(lk_level_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes)) != cudaSuccess) return e;
     return cudaFuncSetAttribute(lk_level_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
 }
 
 cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s) {
+    // Small levels have too few rows to fill the streamed schedule; tiles
+    // run them in one short wave.
+    if (lk_stream_supports(a.iters, a.radius) && (long long)a.w * a.h >= kStreamMinPixels)
+        return launch_lk_stream(a, ndirs, s);
+    return launch_lk_tile(a, ndirs, s);
+}
+
+cudaError_t launch_lk_tile(const LkArgs& a, int ndirs, cudaStream_t s) {
     switch (a.radius) {
         case 1: return launch_rad<1>(a, ndirs, s);
         case 2: return launch_rad<2>(a, ndirs, s);

@@ -14,33 +14,54 @@ namespace {
 constexpr float kInv255 = 1.0f / 255.0f;
 
 // ---------------------------------------------------------------------------
-// Level 0: one thread per pixel. Both strips in one launch (blockIdx.z).
+// Level 0: each thread converts 4 consecutive pixels of one row. Both strips
+// in one launch (blockIdx.z selects the strip; the descriptor is picked with
+// a select, not an indexed parameter load, so it stays in registers).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) luma_kernel(LumaArgs a) {
-    const ImageDesc& in = a.in[blockIdx.z];
-    int x = blockIdx.x * blockDim.x + threadIdx.x;
-    int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= in.w || y >= in.h) return;
-    float v;
+__device__ __forceinline__ float luma_at(const ImageDesc& in, const unsigned char* row, int x) {
     if (in.dtype == 0) {
-        const uint8_t* row = static_cast<const uint8_t*>(in.data) + (long long)y * in.pitch_bytes;
         if (in.c == 3) {
             const uint8_t* px = row + 3 * x;
-            v = (0.299f * px[0] + 0.587f * px[1] + 0.114f * px[2]) * kInv255;
-        } else {
-            v = row[x] * kInv255;
+            return (0.299f * px[0] + 0.587f * px[1] + 0.114f * px[2]) * kInv255;
         }
-    } else {
-        const float* row = reinterpret_cast<const float*>(
-            static_cast<const char*>(in.data) + (long long)y * in.pitch_bytes);
-        if (in.c == 3) {
-            const float* px = row + 3 * x;
-            v = 0.299f * px[0] + 0.587f * px[1] + 0.114f * px[2];
-        } else {
-            v = row[x];
-        }
+        return row[x] * kInv255;
     }
-    a.out[blockIdx.z][(long long)y * a.out_pitch[blockIdx.z] + x] = v;
+    const float* r = reinterpret_cast<const float*>(row);
+    if (in.c == 3) return 0.299f * r[3 * x] + 0.587f * r[3 * x + 1] + 0.114f * r[3 * x + 2];
+    return r[x];
+}
+
+__global__ void __launch_bounds__(256) luma_kernel(LumaArgs a) {
+    const bool second = blockIdx.z != 0;
+    const ImageDesc in = second ? a.in[1] : a.in[0];
+    float* out = second ? a.out[1] : a.out[0];
+    const int out_pitch = second ? a.out_pitch[1] : a.out_pitch[0];
+    const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y;
+    if (x >= in.w || y >= in.h) return;
+    const unsigned char* row = static_cast<const unsigned char*>(in.data) + (long long)y * in.pitch_bytes;
+    float* orow = out + (long long)y * out_pitch;
+    if (x + 4 <= in.w && in.dtype == 0 && in.c == 3 && ((((uintptr_t)row) + 3 * x) & 3) == 0) {
+        // 12 aligned bytes = 4 RGB pixels
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(row + 3 * x);
+        const uint32_t w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2);
+        float v[4];
+        const uint32_t b[12] = {w0 & 255, (w0 >> 8) & 255, (w0 >> 16) & 255, w0 >> 24,
+                                w1 & 255, (w1 >> 8) & 255, (w1 >> 16) & 255, w1 >> 24,
+                                w2 & 255, (w2 >> 8) & 255, (w2 >> 16) & 255, w2 >> 24};
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            v[k] = (0.299f * (float)b[3 * k] + 0.587f * (float)b[3 * k + 1] + 0.114f * (float)b[3 * k + 2]) * kInv255;
+        if ((((uintptr_t)(orow + x)) & 15) == 0) {
+            *reinterpret_cast<float4*>(orow + x) = make_float4(v[0], v[1], v[2], v[3]);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) orow[x + k] = v[k];
+        }
+        return;
+    }
+    const int n = min(4, in.w - x);
+    for (int k = 0; k < n; ++k) orow[x + k] = luma_at(in, row, x + k);
 }
 
 // ---------------------------------------------------------------------------
@@ -56,8 +77,11 @@ constexpr int kPdSH = 2 * kPdTH + 3;
 __global__ void __launch_bounds__(256) pyr_down_kernel(PyrDownArgs a) {
     __shared__ float s_src[kPdSH][kPdSW + 1];
     __shared__ float s_v[kPdTH][kPdSW + 1];
-    const float* __restrict__ src = a.src[blockIdx.z];
-    float* __restrict__ dst = a.dst[blockIdx.z];
+    const bool second = blockIdx.z != 0;
+    const float* __restrict__ src = second ? a.src[1] : a.src[0];
+    float* __restrict__ dst = second ? a.dst[1] : a.dst[0];
+    const int src_pitch = second ? a.src_pitch[1] : a.src_pitch[0];
+    const int dst_pitch = second ? a.dst_pitch[1] : a.dst_pitch[0];
     const int hd = (a.h + 1) >> 1, wd = (a.w + 1) >> 1;
     const int xd0 = blockIdx.x * kPdTW, yd0 = blockIdx.y * kPdTH;
     const int sx0 = 2 * xd0 - 2, sy0 = 2 * yd0 - 2;
@@ -66,7 +90,7 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(PyrDownArgs a) {
         int r = i / kPdSW, c = i - r * kPdSW;
         int sy = min(max(sy0 + r, 0), a.h - 1);
         int sx = min(max(sx0 + c, 0), a.w - 1);
-        s_src[r][c] = __ldg(src + (long long)sy * a.src_pitch[blockIdx.z] + sx);
+        s_src[r][c] = __ldg(src + (long long)sy * src_pitch + sx);
     }
     __syncthreads();
     const float k0 = 1.0f / 16, k1 = 4.0f / 16, k2 = 6.0f / 16;
@@ -81,7 +105,7 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(PyrDownArgs a) {
     if (xd < wd && yd < hd) {
         int c = 2 * threadIdx.x + 2;
         const float* v = s_v[threadIdx.y];
-        dst[(long long)yd * a.dst_pitch[blockIdx.z] + xd] =
+        dst[(long long)yd * dst_pitch + xd] =
             k0 * v[c - 2] + k1 * v[c - 1] + k2 * v[c] + k1 * v[c + 1] + k0 * v[c + 2];
     }
 }
@@ -91,8 +115,8 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(PyrDownArgs a) {
 cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s) {
     int h = max(a.in[0].h, a.count > 1 ? a.in[1].h : 0);
     int w = max(a.in[0].w, a.count > 1 ? a.in[1].w : 0);
-    dim3 block(32, 8);
-    dim3 grid((w + 31) / 32, (h + 7) / 8, a.count);
+    dim3 block(64);
+    dim3 grid((w + 4 * 64 - 1) / (4 * 64), h, a.count);
     luma_kernel<<<grid, block, 0, s>>>(a);
     return cudaGetLastError();
 }
