@@ -135,6 +135,31 @@ __device__ __forceinline__ float2 residual_product(const TargetBox& b, int x, in
     return make_float2(g.x * s, g.y * s);
 }
 
+// Column sums over 2R+1 rows of the product buffer for one column: the
+// CH + 2R values are read once into registers and every output row is summed
+// directly from them (no running sums, which would carry rounding from one
+// row into the next). Also saves the last 2R product rows as the history of
+// this stage for the next chunk.
+template <int RAD, int CH, int RW>
+__device__ __forceinline__ void column_sums(const float2* __restrict__ sP, float2* __restrict__ sV,
+                                            float2* __restrict__ hist, int rx) {
+    float2 p[CH + 2 * RAD];
+#pragma unroll
+    for (int d = 0; d < CH + 2 * RAD; ++d) p[d] = sP[d * RW + rx];
+#pragma unroll
+    for (int yy = 0; yy < CH; ++yy) {
+        float2 v = p[yy];
+#pragma unroll
+        for (int d = 1; d <= 2 * RAD; ++d) {
+            v.x += p[yy + d].x;
+            v.y += p[yy + d].y;
+        }
+        sV[yy * RW + rx] = v;
+    }
+#pragma unroll
+    for (int d = 0; d < 2 * RAD; ++d) hist[d * RW + rx] = p[CH + d];
+}
+
 template <int RAD, int K, int BW, int CH>
 __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, int seg) {
     using Geo = StreamGeom<RAD, K, BW, CH>;
@@ -212,7 +237,15 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
     const int c_first = -((2 * K * RAD + CH - 1) / CH);
     const int c_last = (Y1 - Y0 + CH - 1) / CH - 1;
     stage_inputs(Y0 + K * RAD + c_first * CH);
+    // Rings start at zero: the column sums of the first chunk read ring rows
+    // that no earlier chunk wrote (their results are discarded, but must
+    // stay finite).
     for (int i = tid; i < K * 2 * RAD * RW; i += kStreamThreads) sH[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < kRing * RW; i += kStreamThreads) {
+        sT[i] = 0.f;
+        sG[i] = make_float2(0.f, 0.f);
+        sU[i] = make_float2(0.f, 0.f);
+    }
     {
         // target rows of the first chunk
         const int a0f = Y0 + K * RAD + c_first * CH;
@@ -275,46 +308,36 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
         __syncthreads();
         // the staging buffers are free again: start fetching the next chunk's inputs
         if (c < c_last) stage_inputs(a0 + CH);
-        // ---- B_1: column sums of stage 1 and its history; column sums of
-        //      grad T grad T^T for the normal matrices of rows [a1, a1 + CH)
-        {
-            const int y = a0 - RAD + ty;
-            const float2* pcol = sP + ty * RW;
-            float2* vrow = sV + ty * RW;
-            float2* carow = sCSA + ty * RW;
-            float* cbrow = sCSB + ty * RW;
-            int gslot[2 * RAD + 1];
+        // ---- B_1: column sums of stage 1 (one thread per column, the column's
+        //      values read once into registers) and its history; column sums
+        //      of grad T grad T^T for the normal matrices of rows [a1, a1 + CH)
+        if (tid < RW) {
+            const int rx = tid;
+            const int a1 = a0 - RAD;
+            column_sums<RAD, CH, RW>(sP, sV, sH, rx);
+            int slot[CH + 2 * RAD];
 #pragma unroll
-            for (int d = 0; d <= 2 * RAD; ++d) gslot[d] = ring_slot(y - RAD + d) * RW;
-            for (int rx = tx; rx < RW; rx += TX) {
-                float2 v = pcol[rx];
+            for (int d = 0; d < CH + 2 * RAD; ++d) slot[d] = ring_slot(a1 - RAD + d) * RW + rx;
+            float2 g[CH + 2 * RAD];
 #pragma unroll
-                for (int d = 1; d <= 2 * RAD; ++d) {
-                    const float2 q = pcol[d * RW + rx];
-                    v.x += q.x;
-                    v.y += q.y;
-                }
-                vrow[rx] = v;
-                float g11 = 0.f, g12 = 0.f, g22 = 0.f;
+            for (int d = 0; d < CH + 2 * RAD; ++d) g[d] = sG[slot[d]];
+#pragma unroll
+            for (int yy = 0; yy < CH; ++yy) {
+                float c11 = 0.f, c12 = 0.f, c22 = 0.f;
 #pragma unroll
                 for (int d = 0; d <= 2 * RAD; ++d) {
-                    const float2 g = sG[gslot[d] + rx];
-                    g11 = fmaf(g.x, g.x, g11);
-                    g12 = fmaf(g.x, g.y, g12);
-                    g22 = fmaf(g.y, g.y, g22);
+                    c11 = fmaf(g[yy + d].x, g[yy + d].x, c11);
+                    c12 = fmaf(g[yy + d].x, g[yy + d].y, c12);
+                    c22 = fmaf(g[yy + d].y, g[yy + d].y, c22);
                 }
-                carow[rx] = make_float2(g11, g12);
-                cbrow[rx] = g22;
+                sCSA[yy * RW + rx] = make_float2(c11, c12);
+                sCSB[yy * RW + rx] = c22;
             }
-            for (int i = tid; i < 2 * RAD * RW; i += kStreamThreads) sH[i] = sP[CH * RW + i];
         }
         __syncthreads();
 #pragma unroll
         for (int k = 1; k <= K; ++k) {
             const int c0 = k * RAD;            // columns [c0, RW - c0)
-            const int width = RW - 2 * c0;
-            // items per thread: columns c0 + tx + j TX, j < NI
-            constexpr int NI = (RW + TX - 1) / TX;
             if (k == K) {
                 // target rows that the next chunk's products reach for the
                 // first time: asynchronous copies, issued first so that they
@@ -322,139 +345,117 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
                 const int yj = a0 + CH + box.fref_y + kMY + 1 + ty;
                 const float* jsrc = box.J + (long long)min(max(yj, 0), h - 1) * box.pitchJ;
                 float* jdst = sJ + ring_slot(yj) * JW;
-                for (int bc = tx; bc < JW; bc += TX) {
-                    const unsigned dst = (unsigned)__cvta_generic_to_shared(jdst + bc);
-                    const float* src = jsrc + min(max(jx0 + bc, 0), w - 1);
-                    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
-                }
-                asm volatile("cp.async.commit_group;\n" ::: "memory");
+                for (int bc = tx; bc < JW; bc += TX) copy_async4(jdst + bc, jsrc + min(max(jx0 + bc, 0), w - 1));
+                copy_async_commit();
             }
             // ---- X_k: row sums, solve, update; products of stage k+1
             if (k < K) {
                 const float2* hk = sH + (size_t)k * 2 * RAD * RW;
+                const int width = RW - 2 * c0;
                 for (int i = tid; i < 2 * RAD * width; i += kStreamThreads) {
                     const int yy = i / width, rx = c0 + (i - yy * width);
                     sP[yy * RW + rx] = hk[yy * RW + rx];
                 }
             }
             {
-                const int y = a0 - k * RAD + ty;   // this thread's row of stage k
+                // this thread: row ty of stage k, the column pair (xp, xp + 1)
+                constexpr int HR = (RAD + 1) / 2 * 2;      // even halo >= RAD
+                constexpr int NPAIR = (2 * HR + 2) / 2;     // float4 loads for the row sums
+                const int c0e = c0 & ~1;
+                const int xp = c0e + 2 * tx;
+                const int y = a0 - k * RAD + ty;
                 const bool row_in = y >= 0 && y < h;
-                const int srow = ring_slot(y) * RW;
-                const float2* vrow = sV + ty * RW;
-                const float2* carow = sCSA + ty * RW;
-                const float* cbrow = sCSB + ty * RW;
-                float2* prow = sP + (2 * RAD + ty) * RW;
-                const bool out_row = row_in && y >= Y0 && y < Y1;
-                float2* uo = reinterpret_cast<float2*>(D.uout) + (long long)min(max(y, 0), h - 1) * D.uout_pitch;
-                float2 m[NI], u[NI], ga[NI];
-                float gb[NI];
-                bool on[NI], ins[NI];
-                // 1. all loads of this phase's items
+                const bool on0 = xp >= c0 && xp < RW - c0, on1 = xp + 1 >= c0 && xp + 1 < RW - c0;
+                if (xp < RW - c0) {
+                    const int srow = ring_slot(y) * RW;
+                    const bool in0 = on0 && row_in && xp >= cmin && xp < cmax;
+                    const bool in1 = on1 && row_in && xp + 1 >= cmin && xp + 1 < cmax;
+                    // row sums of the column sums for both pixels
+                    const float4* vq = reinterpret_cast<const float4*>(sV + ty * RW + xp - HR);
+                    float2 vv[2 * HR + 2];
 #pragma unroll
-                for (int j = 0; j < NI; ++j) {
-                    const int rx = c0 + tx + j * TX;
-                    on[j] = rx < RW - c0;
-                    ins[j] = on[j] && row_in && rx >= cmin && rx < cmax;
-                    if (on[j]) {
-                        m[j] = vrow[rx - RAD];
-#pragma unroll
-                        for (int dx = -RAD + 1; dx <= RAD; ++dx) {
-                            const float2 q = vrow[rx + dx];
-                            m[j].x += q.x;
-                            m[j].y += q.y;
-                        }
-                        u[j] = sU[srow + rx];
-                        if (k == 1) {
-                            float g11 = carow[rx - RAD].x, g12 = carow[rx - RAD].y, g22 = cbrow[rx - RAD];
-#pragma unroll
-                            for (int dx = -RAD + 1; dx <= RAD; ++dx) {
-                                g11 += carow[rx + dx].x;
-                                g12 += carow[rx + dx].y;
-                                g22 += cbrow[rx + dx];
-                            }
-                            const float a11 = g11 + lam, a22 = g22 + lam;
-                            const float inv = 1.0f / (a11 * a22 - g12 * g12);
-                            ga[j] = make_float2(a22 * inv, -g12 * inv);
-                            gb[j] = a11 * inv;
-                        } else {
-                            ga[j] = sGiA[srow + rx];
-                            gb[j] = sGiB[srow + rx];
-                        }
+                    for (int q = 0; q < NPAIR; ++q) {
+                        const float4 t4 = vq[q];
+                        vv[2 * q] = make_float2(t4.x, t4.y);
+                        vv[2 * q + 1] = make_float2(t4.z, t4.w);
                     }
-                }
-                // 2. solve and update
-                float2 v[NI];
+                    float2 m0 = vv[HR - RAD], m1 = vv[HR - RAD + 1];
 #pragma unroll
-                for (int j = 0; j < NI; ++j) {
-                    const int rx = c0 + tx + j * TX;
-                    v[j] = make_float2(0.f, 0.f);
-                    if (ins[j]) {
-                        const float r1 = fmaf(lam, u[j].x, m[j].x), r2 = fmaf(lam, u[j].y, m[j].y);
-                        v[j] = make_float2(fmaf(ga[j].x, r1, ga[j].y * r2), fmaf(ga[j].y, r1, gb[j] * r2));
+                    for (int d = 1; d <= 2 * RAD; ++d) {
+                        m0.x += vv[HR - RAD + d].x;
+                        m0.y += vv[HR - RAD + d].y;
+                        m1.x += vv[HR - RAD + d + 1].x;
+                        m1.y += vv[HR - RAD + d + 1].y;
                     }
-                    if (on[j]) {
-                        if (k == 1) {
-                            // inverse normal matrix of this pixel, kept for stages 2..K
-                            sGiA[srow + rx] = ga[j];
-                            sGiB[srow + rx] = gb[j];
+                    float2 ga0, ga1;
+                    float gb0, gb1;
+                    if (k == 1) {
+                        const float2* ca = sCSA + ty * RW + xp;
+                        const float* cb = sCSB + ty * RW + xp;
+                        float a11 = 0.f, a12 = 0.f, a22 = 0.f, b11 = 0.f, b12 = 0.f, b22 = 0.f;
+#pragma unroll
+                        for (int d = -RAD; d <= RAD; ++d) {
+                            a11 += ca[d].x;
+                            a12 += ca[d].y;
+                            a22 += cb[d];
+                            b11 += ca[d + 1].x;
+                            b12 += ca[d + 1].y;
+                            b22 += cb[d + 1];
                         }
-                        if (ins[j]) sU[srow + rx] = v[j];
+                        const float p11 = a11 + lam, p22 = a22 + lam;
+                        const float ip = 1.0f / (p11 * p22 - a12 * a12);
+                        const float q11 = b11 + lam, q22 = b22 + lam;
+                        const float iq = 1.0f / (q11 * q22 - b12 * b12);
+                        ga0 = make_float2(p22 * ip, -a12 * ip);
+                        gb0 = p11 * ip;
+                        ga1 = make_float2(q22 * iq, -b12 * iq);
+                        gb1 = q11 * iq;
+                        *reinterpret_cast<float4*>(sGiA + srow + xp) = make_float4(ga0.x, ga0.y, ga1.x, ga1.y);
+                        *reinterpret_cast<float2*>(sGiB + srow + xp) = make_float2(gb0, gb1);
+                    } else {
+                        const float4 a4 = *reinterpret_cast<const float4*>(sGiA + srow + xp);
+                        const float2 b2 = *reinterpret_cast<const float2*>(sGiB + srow + xp);
+                        ga0 = make_float2(a4.x, a4.y);
+                        ga1 = make_float2(a4.z, a4.w);
+                        gb0 = b2.x;
+                        gb1 = b2.y;
                     }
-                    if (k == K && out_row && ins[j] && rx >= K * RAD && rx < K * RAD + BW)
-                        uo[ox + rx] = make_float2(v[j].x + ref.x, v[j].y + ref.y);
-                }
-                // 3. products of stage k+1
-                if (k < K) {
-                    float2 g[NI];
-                    float t[NI];
-#pragma unroll
-                    for (int j = 0; j < NI; ++j) {
-                        const int rx = c0 + tx + j * TX;
-                        if (ins[j]) {
-                            g[j] = sG[srow + rx];
-                            t[j] = sT[srow + rx];
+                    const float4 u4 = *reinterpret_cast<const float4*>(sU + srow + xp);
+                    float2 v0 = make_float2(u4.x, u4.y), v1 = make_float2(u4.z, u4.w);
+                    if (in0) {
+                        const float r1 = fmaf(lam, v0.x, m0.x), r2 = fmaf(lam, v0.y, m0.y);
+                        v0 = make_float2(fmaf(ga0.x, r1, ga0.y * r2), fmaf(ga0.y, r1, gb0 * r2));
+                    }
+                    if (in1) {
+                        const float r1 = fmaf(lam, v1.x, m1.x), r2 = fmaf(lam, v1.y, m1.y);
+                        v1 = make_float2(fmaf(ga1.x, r1, ga1.y * r2), fmaf(ga1.y, r1, gb1 * r2));
+                    }
+                    *reinterpret_cast<float4*>(sU + srow + xp) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                    if (k == K) {
+                        if (row_in && y >= Y0 && y < Y1) {
+                            float2* uo = reinterpret_cast<float2*>(D.uout) + (long long)y * D.uout_pitch;
+                            if (in0 && xp >= K * RAD && xp < K * RAD + BW)
+                                uo[ox + xp] = make_float2(v0.x + ref.x, v0.y + ref.y);
+                            if (in1 && xp + 1 >= K * RAD && xp + 1 < K * RAD + BW)
+                                uo[ox + xp + 1] = make_float2(v1.x + ref.x, v1.y + ref.y);
                         }
-                    }
-#pragma unroll
-                    for (int j = 0; j < NI; ++j) {
-                        const int rx = c0 + tx + j * TX;
-                        float2 P = make_float2(0.f, 0.f);
-                        if (ins[j]) P = residual_product<JW>(box, ox + rx, y, rx, ref, v[j], g[j], t[j]);
-                        if (on[j]) prow[rx] = P;
+                    } else {
+                        // products of stage k+1 at the same two pixels
+                        const float4 g4 = *reinterpret_cast<const float4*>(sG + srow + xp);
+                        const float2 t2 = *reinterpret_cast<const float2*>(sT + srow + xp);
+                        float2 P0 = make_float2(0.f, 0.f), P1 = make_float2(0.f, 0.f);
+                        if (in0) P0 = residual_product<JW>(box, ox + xp, y, xp, ref, v0, make_float2(g4.x, g4.y), t2.x);
+                        if (in1) P1 = residual_product<JW>(box, ox + xp + 1, y, xp + 1, ref, v1, make_float2(g4.z, g4.w), t2.y);
+                        *reinterpret_cast<float4*>(sP + (2 * RAD + ty) * RW + xp) = make_float4(P0.x, P0.y, P1.x, P1.y);
                     }
                 }
             }
-            if (k == K) asm volatile("cp.async.wait_all;\n" ::: "memory");
+            if (k == K) copy_async_wait_all();
             __syncthreads();
             if (k < K) {
                 // ---- B_{k+1}: column sums of stage k+1 and its history
-                float2* hk = sH + (size_t)k * 2 * RAD * RW;
-                const float2* pcol = sP + ty * RW;
-                float2* vrow = sV + ty * RW;
-                float2 acc[NI];
-#pragma unroll
-                for (int j = 0; j < NI; ++j) {
-                    const int rx = c0 + tx + j * TX;
-                    if (rx < RW - c0) {
-                        acc[j] = pcol[rx];
-#pragma unroll
-                        for (int d = 1; d <= 2 * RAD; ++d) {
-                            const float2 q = pcol[d * RW + rx];
-                            acc[j].x += q.x;
-                            acc[j].y += q.y;
-                        }
-                    }
-                }
-#pragma unroll
-                for (int j = 0; j < NI; ++j) {
-                    const int rx = c0 + tx + j * TX;
-                    if (rx < RW - c0) vrow[rx] = acc[j];
-                }
-                for (int i = tid; i < 2 * RAD * width; i += kStreamThreads) {
-                    const int yy = i / width, rx = c0 + (i - yy * width);
-                    hk[yy * RW + rx] = sP[(CH + yy) * RW + rx];
-                }
+                const int rx = c0 + tid;
+                if (rx < RW - c0) column_sums<RAD, CH, RW>(sP, sV, sH + (size_t)k * 2 * RAD * RW, rx);
                 __syncthreads();
             }
         }
