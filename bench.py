@@ -34,6 +34,11 @@ UNIT = "MP/s"
 WORKLOAD = {"workload": "pair_4000x1500_rgb_u8_lv6", "h": 4000, "w": 1500, "channels": 3, "levels": 6,
             "iters": 5, "radius": 2}
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
+STREAM_MIN_PIXELS = 100000   # levels with at least this many pixels use the streamed LK kernel
+# DRAM bytes (read + write) per launch of the dominant kernel, averaged over
+# its launches in one step, from an ncu capture of the current kernel; None
+# when the kernel has changed since the counters were taken.
+TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (171.124e6 + 4.653e6 + 18.478e6) / 3}
 
 
 # ---------------------------------------------------------------------------
@@ -285,10 +290,20 @@ def run_gpu(args):
     torch.cuda.synchronize()
     recs = ctx.trace_read(64 * args.steps)
     ctx.trace_enable(0, 0)
-    names = {1: "luma_kernel", 2: "pyr_down_kernel", 4: "lk_level_kernel", 8: "blend_kernel"}
+    names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "blend_kernel"}
+    npx = level_pixels(h, w, levels)
+    lk_bytes = lk_alg_bytes(h, w, levels)
     per_kind = {}
+    stream_bytes = 0.0
     for kind, lev, ms in recs:
-        d = per_kind.setdefault(names[kind], {"launches": 0, "ms": 0.0})
+        if kind == 4:
+            # levels of at least STREAM_MIN_PIXELS run the streamed kernel
+            name = "lk_stream_kernel" if npx[lev] >= STREAM_MIN_PIXELS else "lk_level_kernel"
+            if name == "lk_stream_kernel":
+                stream_bytes += lk_bytes[lev]
+        else:
+            name = names[kind]
+        d = per_kind.setdefault(name, {"launches": 0, "ms": 0.0})
         d["launches"] += 1
         d["ms"] += ms
     traced_total = sum(d["ms"] for d in per_kind.values())
@@ -296,14 +311,20 @@ def run_gpu(args):
         d["share"] = d["ms"] / traced_total if traced_total else None
         d["ms_per_step"] = d["ms"] / args.steps
     dominant = max(per_kind, key=lambda k: per_kind[k]["ms"])
-    lk_bytes_step = sum(lk_alg_bytes(h, w, levels))
-    lk_ms_step = per_kind["lk_level_kernel"]["ms"] / args.steps
+    dk = per_kind[dominant]
+    launches_per_step = dk["launches"] / args.steps
+    if dominant == "lk_stream_kernel":
+        bytes_per_launch = stream_bytes / dk["launches"]
+    else:
+        bytes_per_launch = None
     peak, peak_src = read_peaks()
-    achieved = lk_bytes_step / (lk_ms_step * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "kernel": "lk_level_kernel",
-                "alg_bytes_per_launch": lk_bytes_step / levels, "launch_ms": lk_ms_step / levels,
-                "peak_source": f"{peak_src} hbm_gbs"}
+    launch_ms = dk["ms"] / dk["launches"]
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9 if bytes_per_launch else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": TRAFFIC_PER_LAUNCH.get(dominant), "kernel": dominant,
+                "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
+                "launches_per_step": launches_per_step, "peak_source": f"{peak_src} hbm_gbs"}
     path_bytes = path_alg_bytes(h, w, c, levels)
     path_gbs = path_bytes / (total_ms / args.steps * 1e-3) / 1e9
 

@@ -42,6 +42,7 @@ constexpr int kRing = 32;
 constexpr int kRingOff = 1 << 20;  // keeps ring slots of negative rows non-negative
 constexpr int kMX = 8;             // target box margin, columns
 constexpr int kMY = 3;             // target box margin, rows
+constexpr int kCsT0 = 256;         // first thread of the normal-matrix column sums in B_1
 
 template <int RAD, int K, int BW, int CH>
 struct StreamGeom {
@@ -169,6 +170,7 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
     // block of rows and on the columns tx, tx + TX, tx + 2 TX, ...
     constexpr int TX = kStreamThreads / CH;
     static_assert(TX * CH == kStreamThreads, "threads must tile the chunk rows");
+    static_assert(RW <= kCsT0 && kCsT0 + 2 * RW <= kStreamThreads && CH % 2 == 0, "B_1 thread groups");
     extern __shared__ __align__(16) unsigned char smem[];
     float* sT = reinterpret_cast<float*>(smem + Geo::kT);
     float2* sG = reinterpret_cast<float2*>(smem + Geo::kG);
@@ -312,17 +314,17 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
         //      values read once into registers) and its history; column sums
         //      of grad T grad T^T for the normal matrices of rows [a1, a1 + CH)
         if (tid < RW) {
-            const int rx = tid;
-            const int a1 = a0 - RAD;
-            column_sums<RAD, CH, RW>(sP, sV, sH, rx);
-            int slot[CH + 2 * RAD];
+            column_sums<RAD, CH, RW>(sP, sV, sH, tid);
+        } else if (tid >= kCsT0 && tid < kCsT0 + 2 * RW) {
+            // normal-matrix column sums: two threads per column, CH/2 rows each
+            const int rx = (tid - kCsT0) % RW, half = (tid - kCsT0) / RW;
+            constexpr int HC = CH / 2;
+            const int yb = a0 - 2 * RAD + half * HC;   // first ring row of this half's windows
+            float2 g[HC + 2 * RAD];
 #pragma unroll
-            for (int d = 0; d < CH + 2 * RAD; ++d) slot[d] = ring_slot(a1 - RAD + d) * RW + rx;
-            float2 g[CH + 2 * RAD];
+            for (int d = 0; d < HC + 2 * RAD; ++d) g[d] = sG[ring_slot(yb + d) * RW + rx];
 #pragma unroll
-            for (int d = 0; d < CH + 2 * RAD; ++d) g[d] = sG[slot[d]];
-#pragma unroll
-            for (int yy = 0; yy < CH; ++yy) {
+            for (int yy = 0; yy < HC; ++yy) {
                 float c11 = 0.f, c12 = 0.f, c22 = 0.f;
 #pragma unroll
                 for (int d = 0; d <= 2 * RAD; ++d) {
@@ -330,8 +332,9 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
                     c12 = fmaf(g[yy + d].x, g[yy + d].y, c12);
                     c22 = fmaf(g[yy + d].y, g[yy + d].y, c22);
                 }
-                sCSA[yy * RW + rx] = make_float2(c11, c12);
-                sCSB[yy * RW + rx] = c22;
+                const int o = (half * HC + yy) * RW + rx;
+                sCSA[o] = make_float2(c11, c12);
+                sCSB[o] = c22;
             }
         }
         __syncthreads();
@@ -467,7 +470,8 @@ cudaError_t launch_one(const LkArgs& a, int ndirs, cudaStream_t s) {
     using Geo = StreamGeom<RAD, K, BW, CH>;
     const int nb = (a.w + BW - 1) / BW;
     const int per_row = nb * ndirs;
-    // segments: about 192+ rows each, in whole waves of one CTA per SM
+    // segments of about 192+ rows (the first chunks of a segment are
+    // discarded work), in whole waves of one CTA per SM
     const int sms = 152;
     long long waves = (long long)per_row * a.h / (192LL * sms);
     if (waves < 1) waves = 1;
