@@ -1,0 +1,71 @@
+"""Host-side logic of bench.py: byte models, whole-job throughput and the
+multi-rank timing reduction (world_size 2, gloo, on CPU)."""
+import os
+import socket
+
+import pytest
+
+import bench
+
+
+def test_level_pixels_and_lk_bytes():
+    assert bench.level_pixels(4000, 1500, 3) == [6_000_000, 1_500_000, 375_000]
+    b = bench.lk_alg_bytes(4000, 1500, 2)
+    # level 0: 2 directions x (T + J 8 B, coarse flow 8 B per coarse pixel, flow out 8 B)
+    assert b[0] == 2 * (8 * 6_000_000 + 8 * 1_500_000 + 8 * 6_000_000)
+    assert b[1] == 2 * (8 * 1_500_000 + 8 * 1_500_000)
+
+
+def test_throughput_counts_every_rank():
+    # 6 MP per step, 10 steps, 2 ranks, slowest rank 20 ms in total
+    assert bench.throughput(6_000_000, 10, 2, 20.0) == pytest.approx(6000.0)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    try:
+        bench.barrier(world)
+        total_ms = 10.0 + 5.0 * rank          # rank 1 is slower
+        m = bench.reduce_max(total_ms, world)
+        value = bench.throughput(1_000_000, 4, world, m)
+        q.put((rank, m, value, bench.dist_env()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_reduce_max_and_barrier_over_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    res = sorted(q.get(timeout=10) for _ in range(2))
+    for rank, m, value, env in res:
+        assert m == 15.0                       # max over ranks
+        assert value == pytest.approx(1_000_000 * 4 * 2 / 15e-3 / 1e6)
+        assert env[0] == rank and env[1] == 2
+
+
+def test_reference_arm_on_nonzero_rank_exits_quietly(monkeypatch, capsys):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    assert bench.main(["--impl", "reference", "--steps", "1", "--warmup", "3"]) == 0
+    assert capsys.readouterr().out == ""
+
+
+def test_warmup_below_three_is_rejected():
+    with pytest.raises(SystemExit):
+        bench.main(["--warmup", "2"])
