@@ -146,6 +146,33 @@ PANO_API pano_status pano_flow_destroy(pano_flow_ctx* ctx);
 PANO_API const char* pano_last_error(const pano_flow_ctx* ctx);
 
 /* ----------------------------------------------------------------------
+ * Differentiable refinement. Not a step of the paper: a build extension
+ * that refines a flow by gradient steps on the energy
+ *   E(u) = sum_p (J(p + u(p)) - T(p))^2
+ *        + alpha sum_p sum_c [(u_c(p + e_x) - u_c(p))^2 [x < w-1] + (u_c(p + e_y) - u_c(p))^2 [y < h-1]]
+ * i.e. the data term of the flow step plus the smoothness term of the
+ * Horn-Schunck half of the reference the paper cites for LK ([20]). J is
+ * sampled with the bilinear clamp-to-edge sampler of the flow path.
+ * ---------------------------------------------------------------------- */
+
+/* E and its gradients for template T and target J (h x w float32, row pitch
+ * `pitch` floats) and flow u ((h, w, 2) float32 contiguous).
+ * energy: device pointer to one double that receives E (reduced in FP64), or
+ * NULL. grad_u ((h, w, 2)), grad_T ((h, w)) and grad_J ((h, w)), all float32
+ * contiguous, receive dE/du, dE/dT and dE/dJ; any may be NULL. dE/dJ is
+ * accumulated with atomic additions, so its last bits vary between runs.
+ * Errors: INVALID_ARG, CUDA. */
+PANO_API pano_status pano_energy_grad(const float* T, const float* J, int h, int w, int pitch, const float* u,
+                                      float alpha, double* energy, float* grad_u, float* grad_T, float* grad_J,
+                                      void* cuda_stream);
+
+/* Transpose of pano_stage_pyr_down: given the gradient gdst of the
+ * ceil(h/2) x ceil(w/2) output (row pitch dst_pitch), writes the gradient
+ * gsrc of the h x w input (row pitch src_pitch). Errors: INVALID_ARG, CUDA. */
+PANO_API pano_status pano_stage_pyr_down_adjoint(const float* gdst, int h, int w, int dst_pitch, float* gsrc,
+                                                 int src_pitch, void* cuda_stream);
+
+/* ----------------------------------------------------------------------
  * Flow without any device allocation. (The paper has no counterpart: this is
  * a deployment variant of pano_flow_pair.)
  *

@@ -69,6 +69,9 @@ def lib():
             "oracle_blend": ([_D, _D, i, i, i, _D, _D, _D, d, d, _D], None),
             "oracle_blend_weights": ([i, i, _D, _D, _D, d, d, _D, _D], None),
             "oracle_quantize_u8": ([_D, l, _U8], None),
+            "oracle_energy": ([_D, _D, i, i, _D, d], d),
+            "oracle_energy_grad": ([_D, _D, i, i, _D, d, _D, _D, _D], None),
+            "oracle_pyr_down_adjoint": ([_D, i, i, _D], None),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -280,3 +283,32 @@ def stitch_pair(L: np.ndarray, R: np.ndarray, p: Params, blend_arr=None):
     if L.dtype == np.uint8:
         F = quantize_u8(F)
     return lr, rl, F
+
+
+# ---------------------------------------------------------------------------
+# differentiable refinement (energy, its gradients, REDUCE transpose)
+# ---------------------------------------------------------------------------
+
+def energy(T, J, u, alpha: float) -> float:
+    t, j, uu = _f64(T), _f64(J), _f64(u)
+    h, w = t.shape
+    return float(lib().oracle_energy(_d(t), _d(j), h, w, _d(uu), float(alpha)))
+
+
+def energy_grad(T, J, u, alpha: float):
+    """(dE/du (h, w, 2), dE/dT (h, w), dE/dJ (h, w))."""
+    t, j, uu = _f64(T), _f64(J), _f64(u)
+    h, w = t.shape
+    gu = np.empty((h, w, 2))
+    gt = np.empty((h, w))
+    gj = np.empty((h, w))
+    lib().oracle_energy_grad(_d(t), _d(j), h, w, _d(uu), float(alpha), _d(gu), _d(gt), _d(gj))
+    return gu, gt, gj
+
+
+def pyr_down_adjoint(gdst: np.ndarray, h: int, w: int) -> np.ndarray:
+    g = _f64(gdst)
+    assert g.shape == ((h + 1) // 2, (w + 1) // 2)
+    out = np.empty((h, w))
+    lib().oracle_pyr_down_adjoint(_d(g), h, w, _d(out))
+    return out

@@ -464,3 +464,116 @@ void oracle_quantize_u8(const double* F, long n, unsigned char* out)
         out[i] = (unsigned char)v;
     }
 }
+
+/* ===========================================================================
+ * Differentiable refinement (not in the paper: a build extension whose
+ * energy takes its smoothness term from the Horn-Schunck half of [20]).
+ *
+ *   E(u) = sum_p (J(p + u(p)) - T(p))^2
+ *        + alpha sum_p sum_{c in {x,y}} [ (u_c(p + e_x) - u_c(p))^2 [x < w-1]
+ *                                       + (u_c(p + e_y) - u_c(p))^2 [y < h-1] ]
+ * with J sampled bilinearly with clamp-to-edge taps (the sampler of the LK
+ * step) and forward differences that are zero across the image border.
+ * ========================================================================= */
+
+/* Bilinear sample and its derivative with respect to the sample position,
+   taps clamped to the image (the derivative is that of the interpolant). */
+static double bilinear_d(const double* I, int h, int w, double x, double y, double* dx, double* dy)
+{
+    double x0f = floor(x), y0f = floor(y);
+    double fx = x - x0f, fy = y - y0f;
+    if (x0f < -2.0) x0f = -2.0;
+    if (x0f > (double)w + 1.0) x0f = (double)w + 1.0;
+    if (y0f < -2.0) y0f = -2.0;
+    if (y0f > (double)h + 1.0) y0f = (double)h + 1.0;
+    int x0 = (int)x0f, y0 = (int)y0f;
+    int xa = clampi(x0, 0, w - 1), xb = clampi(x0 + 1, 0, w - 1);
+    int ya = clampi(y0, 0, h - 1), yb = clampi(y0 + 1, 0, h - 1);
+    double i00 = PIX(I, w, ya, xa), i10 = PIX(I, w, ya, xb);
+    double i01 = PIX(I, w, yb, xa), i11 = PIX(I, w, yb, xb);
+    *dx = (1.0 - fy) * (i10 - i00) + fy * (i11 - i01);
+    *dy = (1.0 - fx) * (i01 - i00) + fx * (i11 - i10);
+    return (1.0 - fy) * ((1.0 - fx) * i00 + fx * i10) + fy * ((1.0 - fx) * i01 + fx * i11);
+}
+
+double oracle_energy(const double* T, const double* J, int h, int w, const double* u, double alpha)
+{
+    double data = 0.0, smooth = 0.0;
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            size_t p = (size_t)y * w + x;
+            double r = bilinear_strided(J, h, w, 1, x + u[2 * p], y + u[2 * p + 1]) - T[p];
+            data += r * r;
+            for (int c = 0; c < 2; ++c) {
+                if (x < w - 1) { double d = u[2 * (p + 1) + c] - u[2 * p + c]; smooth += d * d; }
+                if (y < h - 1) { double d = u[2 * (p + w) + c] - u[2 * p + c]; smooth += d * d; }
+            }
+        }
+    return data + alpha * smooth;
+}
+
+/* Gradients of oracle_energy: gu (h, w, 2), gT (h, w), gJ (h, w); any may be
+   NULL. dE/dJ collects 2 r(p) times each tap's bilinear weight at the tap's
+   clamped position. */
+void oracle_energy_grad(const double* T, const double* J, int h, int w, const double* u, double alpha,
+                        double* gu, double* gT, double* gJ)
+{
+    size_t n = (size_t)h * w;
+    if (gJ) memset(gJ, 0, n * sizeof(double));
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            size_t p = (size_t)y * w + x;
+            double sx = x + u[2 * p], sy = y + u[2 * p + 1];
+            double jdx, jdy;
+            double r = bilinear_d(J, h, w, sx, sy, &jdx, &jdy) - T[p];
+            if (gu) {
+                gu[2 * p + 0] = 2.0 * r * jdx;
+                gu[2 * p + 1] = 2.0 * r * jdy;
+                for (int c = 0; c < 2; ++c) {
+                    double s = 0.0;
+                    if (x > 0) s += u[2 * p + c] - u[2 * (p - 1) + c];
+                    if (x < w - 1) s += u[2 * p + c] - u[2 * (p + 1) + c];
+                    if (y > 0) s += u[2 * p + c] - u[2 * (p - w) + c];
+                    if (y < h - 1) s += u[2 * p + c] - u[2 * (p + w) + c];
+                    gu[2 * p + c] += 2.0 * alpha * s;
+                }
+            }
+            if (gT) gT[p] = -2.0 * r;
+            if (gJ) {
+                double x0f = floor(sx), y0f = floor(sy);
+                double fx = sx - x0f, fy = sy - y0f;
+                if (x0f < -2.0) x0f = -2.0;
+                if (x0f > (double)w + 1.0) x0f = (double)w + 1.0;
+                if (y0f < -2.0) y0f = -2.0;
+                if (y0f > (double)h + 1.0) y0f = (double)h + 1.0;
+                int x0 = (int)x0f, y0 = (int)y0f;
+                int xa = clampi(x0, 0, w - 1), xb = clampi(x0 + 1, 0, w - 1);
+                int ya = clampi(y0, 0, h - 1), yb = clampi(y0 + 1, 0, h - 1);
+                double g = 2.0 * r;
+                PIX(gJ, w, ya, xa) += g * (1.0 - fy) * (1.0 - fx);
+                PIX(gJ, w, ya, xb) += g * (1.0 - fy) * fx;
+                PIX(gJ, w, yb, xa) += g * fy * (1.0 - fx);
+                PIX(gJ, w, yb, xb) += g * fy * fx;
+            }
+        }
+}
+
+/* Transpose of oracle_pyr_down: given the gradient of the (ceil(h/2),
+   ceil(w/2)) output, the gradient of the (h, w) input. Each output pixel
+   spreads its value back along the same 5x5 binomial weights and clamped
+   taps that formed it. */
+void oracle_pyr_down_adjoint(const double* gdst, int h, int w, double* gsrc)
+{
+    static const double k[5] = {1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16};
+    int hd = (h + 1) / 2, wd = (w + 1) / 2;
+    memset(gsrc, 0, (size_t)h * w * sizeof(double));
+    for (int yd = 0; yd < hd; ++yd)
+        for (int xd = 0; xd < wd; ++xd) {
+            double g = PIX(gdst, wd, yd, xd);
+            for (int ty = -2; ty <= 2; ++ty)
+                for (int tx = -2; tx <= 2; ++tx) {
+                    int sy = clampi(2 * yd + ty, 0, h - 1), sx = clampi(2 * xd + tx, 0, w - 1);
+                    PIX(gsrc, w, sy, sx) += k[ty + 2] * k[tx + 2] * g;
+                }
+        }
+}

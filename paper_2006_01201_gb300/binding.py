@@ -63,6 +63,8 @@ SIGNATURES = {
     "pano_trace_read": ([_VP, ctypes.POINTER(PanoTraceRecord), _I, ctypes.POINTER(ctypes.c_int)], _I),
     "pano_flow_launches": ([_VP], ctypes.c_ulonglong),
     "pano_flow_pair_static": ([_PAR, _IMG, _IMG, _VP, _VP, _VP], _I),
+    "pano_energy_grad": ([_VP, _VP, _I, _I, _I, _VP, _F, _VP, _VP, _VP, _VP, _VP], _I),
+    "pano_stage_pyr_down_adjoint": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
     "pano_stage_luma": ([_IMG, _VP, _I, _VP], _I),
     "pano_stage_pyr_down": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
     "pano_stage_lk": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _VP], _I),
@@ -340,3 +342,33 @@ def stage_warp(src, flow, scale=1.0, stream=None):
     _check(load_library().pano_stage_warp(ctypes.byref(d), _flow_ptr(flow, d.h, d.w, "flow"), float(scale),
                                           ctypes.byref(dd), _stream_ptr(stream)))
     return dst
+
+
+def energy_grad(T, J, u, alpha: float, want_energy=True, want_u=True, want_T=True, want_J=True, stream=None):
+    """(E as a float64 0-d tensor or None, dE/du, dE/dT, dE/dJ) on the GPU."""
+    torch = _torch()
+    for t, n in ((T, "T"), (J, "J")):
+        if t.dtype != torch.float32 or t.dim() != 2 or not t.is_contiguous():
+            raise PanoError(PANO_ERR_INVALID_ARG, f"{n} must be a contiguous float32 (H, W) tensor")
+    h, w = T.shape
+    uptr = _flow_ptr(u, h, w, "u")
+    dev = T.device
+    E = torch.empty((), dtype=torch.float64, device=dev) if want_energy else None
+    gu = torch.empty((h, w, 2), dtype=torch.float32, device=dev) if want_u else None
+    gt = torch.empty((h, w), dtype=torch.float32, device=dev) if want_T else None
+    gj = torch.empty((h, w), dtype=torch.float32, device=dev) if want_J else None
+    ptr = lambda t: None if t is None else t.data_ptr()
+    _check(load_library().pano_energy_grad(T.data_ptr(), J.data_ptr(), h, w, w, uptr, float(alpha), ptr(E),
+                                           ptr(gu), ptr(gt), ptr(gj), _stream_ptr(stream)))
+    return E, gu, gt, gj
+
+
+def stage_pyr_down_adjoint(gdst, h: int, w: int, stream=None):
+    """Gradient of the (h, w) input of a REDUCE from the gradient of its output."""
+    torch = _torch()
+    if gdst.dtype != torch.float32 or tuple(gdst.shape) != ((h + 1) // 2, (w + 1) // 2) or not gdst.is_contiguous():
+        raise PanoError(PANO_ERR_INVALID_ARG, "gdst must be a contiguous float32 (ceil(h/2), ceil(w/2)) tensor")
+    out = torch.empty((h, w), dtype=torch.float32, device=gdst.device)
+    _check(load_library().pano_stage_pyr_down_adjoint(gdst.data_ptr(), h, w, gdst.shape[1], out.data_ptr(), w,
+                                                      _stream_ptr(stream)))
+    return out

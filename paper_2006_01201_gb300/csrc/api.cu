@@ -558,4 +558,41 @@ pano_status pano_stage_warp(const pano_image* src, const float* flow, float scal
     return e == cudaSuccess ? PANO_OK : cuda_fail(e, "warp launch");
 }
 
+pano_status pano_energy_grad(const float* T, const float* J, int h, int w, int pitch, const float* u, float alpha,
+                             double* energy, float* grad_u, float* grad_T, float* grad_J, void* cuda_stream) {
+    if (!T || !J || !u) return fail(PANO_ERR_INVALID_ARG, "T, J or u is NULL");
+    if (h < 1 || w < 1 || pitch < w) return fail(PANO_ERR_INVALID_ARG, "bad size or pitch");
+    if (((uintptr_t)T) % 4 || ((uintptr_t)J) % 4 || ((uintptr_t)u) % 8)
+        return fail(PANO_ERR_INVALID_ARG, "T, J or u misaligned");
+    if ((energy && ((uintptr_t)energy) % 8) || (grad_u && ((uintptr_t)grad_u) % 8) ||
+        (grad_T && ((uintptr_t)grad_T) % 4) || (grad_J && ((uintptr_t)grad_J) % 4))
+        return fail(PANO_ERR_INVALID_ARG, "output misaligned");
+    if (!(alpha >= 0.f) || !(alpha < 1e30f)) return fail(PANO_ERR_INVALID_ARG, "alpha must be finite and >= 0");
+    if ((double)h * (double)pitch > (double)INT_MAX) return fail(PANO_ERR_UNSUPPORTED, "more than 2^31 elements");
+    EnergyArgs a;
+    a.T = T;
+    a.J = J;
+    a.u = u;
+    a.h = h;
+    a.w = w;
+    a.pitch = pitch;
+    a.alpha = alpha;
+    a.energy = energy;
+    a.grad_u = grad_u;
+    a.grad_T = grad_T;
+    a.grad_J = grad_J;
+    cudaError_t e = launch_energy_grad(a, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? PANO_OK : cuda_fail(e, "energy launch");
+}
+
+pano_status pano_stage_pyr_down_adjoint(const float* gdst, int h, int w, int dst_pitch, float* gsrc, int src_pitch,
+                                        void* cuda_stream) {
+    if (!gdst || !gsrc || ((uintptr_t)gdst) % 4 || ((uintptr_t)gsrc) % 4)
+        return fail(PANO_ERR_INVALID_ARG, "gdst or gsrc NULL or misaligned");
+    if (h < 1 || w < 1 || src_pitch < w || dst_pitch < (w + 1) / 2)
+        return fail(PANO_ERR_INVALID_ARG, "bad size or pitch");
+    cudaError_t e = launch_pyr_down_adjoint(gdst, h, w, dst_pitch, gsrc, src_pitch, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? PANO_OK : cuda_fail(e, "REDUCE adjoint launch");
+}
+
 }  // extern "C"

@@ -128,6 +128,19 @@ struct WarpArgs {
     long long dst_pitch_bytes;
 };
 
+// Energy and gradients of the differentiable refinement (refine.cu).
+struct EnergyArgs {
+    const float* T;
+    const float* J;
+    const float* u;      // (h, w, 2)
+    int h, w, pitch;     // pitch of T and J in floats
+    float alpha;
+    double* energy;      // one double, or null
+    float* grad_u;       // (h, w, 2) or null
+    float* grad_T;       // (h, w) or null
+    float* grad_J;       // (h, w) or null (zeroed by the launcher)
+};
+
 // Launchers: enqueue on `s`, return the launch error (cudaSuccess if none).
 cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s);
 cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s);
@@ -144,6 +157,10 @@ size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius);
 cudaError_t lk_prepare(int max_smem_bytes);
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
 cudaError_t launch_warp(const WarpArgs& a, cudaStream_t s);
+
+cudaError_t launch_energy_grad(const EnergyArgs& a, cudaStream_t s);
+cudaError_t launch_pyr_down_adjoint(const float* gdst, int h, int w, int dst_pitch, float* gsrc, int src_pitch,
+                                    cudaStream_t s);
 
 // Stores the message that pano_last_error() returns on the calling thread.
 void set_last_error(const char* msg);

@@ -13,6 +13,7 @@ import pytest
 
 import oracle
 from tests import test_oracle_pins as pins
+from tests import test_oracle_refine_pins as rpins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "pano_oracle.c")
 
@@ -26,9 +27,11 @@ MUTANTS = [
     ("window clamped not clipped", "if (qx < 0 || qx >= w) continue;", "if (0) continue;"),
     ("upsample not doubled", "uf[2 * p + 0] = 2.0 *", "uf[2 * p + 0] = 1.0 *"),
     ("upsample wrong scale", "0.5 * x, 0.5 * y);\n            uf[2 * p + 1]", "0.5 * x, 0.5 * x);\n            uf[2 * p + 1]"),
-    ("pyramid odd kernel", "{1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16}", "{1.0 / 16, 4.0 / 16, 6.0 / 16, 5.0 / 16, 0.0 / 16}"),
+    ("pyramid odd kernel", "{1.0 / 16, 4.0 / 16, 6.0 / 16, 4.0 / 16, 1.0 / 16};\n    int hd = (h + 1) / 2, wd = (w + 1) / 2;\n    double* tmp",
+     "{1.0 / 16, 4.0 / 16, 6.0 / 16, 5.0 / 16, 0.0 / 16};\n    int hd = (h + 1) / 2, wd = (w + 1) / 2;\n    double* tmp"),
     ("pyramid keeps odd rows", "int y = 2 * yd, x = 2 * xd;", "int y = 2 * yd + 1, x = 2 * xd;"),
-    ("bilinear fx/fy swapped", "(1.0 - fy) * ((1.0 - fx) * i00 + fx * i10)", "(1.0 - fx) * ((1.0 - fy) * i00 + fy * i10)"),
+    ("bilinear fx/fy swapped", "return (1.0 - fy) * ((1.0 - fx) * i00 + fx * i10) + fy * ((1.0 - fx) * i01 + fx * i11);\n}\n\ndouble oracle_bilinear(",
+     "return (1.0 - fx) * ((1.0 - fy) * i00 + fy * i10) + fy * ((1.0 - fx) * i01 + fx * i11);\n}\n\ndouble oracle_bilinear("),
     ("gradient halved twice", "PIX(Ix, w, y, x) = 0.5 *", "PIX(Ix, w, y, x) = 0.25 *"),
     ("luma weights", "0.299 * img[3 * i + 0] + 0.587", "0.587 * img[3 * i + 0] + 0.299"),
     ("blend position uses BlendL", "double Lx = x + rlx * (1.0 - blendL)", "double Lx = x + rlx * blendL"),
@@ -39,6 +42,15 @@ MUTANTS = [
     ("Eq1 ramp off by one", "out[x] = (double)(x + 1) / (double)(w + 1);", "out[x] = (double)(x) / (double)(w + 1);"),
     ("Eq1 distance squared", "double d = sqrt(", "double d = ("),
     ("quantize truncates", "double v = nearbyint(255.0 * F[i]);", "double v = floor(255.0 * F[i]);"),
+    ("energy smoothness one-sided", "if (y < h - 1) { double d = u[2 * (p + w) + c] - u[2 * p + c]; smooth += d * d; }",
+     "if (0) { double d = 0; smooth += d * d; }"),
+    ("energy grad drops factor 2", "gu[2 * p + c] += 2.0 * alpha * s;", "gu[2 * p + c] += alpha * s;"),
+    ("energy grad T sign", "if (gT) gT[p] = -2.0 * r;", "if (gT) gT[p] = 2.0 * r;"),
+    ("energy grad J tap weight", "PIX(gJ, w, ya, xb) += g * (1.0 - fy) * fx;", "PIX(gJ, w, ya, xb) += g * fy * fx;"),
+    ("energy grad derivative axis", "*dx = (1.0 - fy) * (i10 - i00) + fy * (i11 - i01);",
+     "*dx = (1.0 - fx) * (i10 - i00) + fx * (i11 - i01);"),
+    ("reduce adjoint weight", "PIX(gsrc, w, sy, sx) += k[ty + 2] * k[tx + 2] * g;",
+     "PIX(gsrc, w, sy, sx) += k[ty + 2] * k[ty + 2] * g;"),
 ]
 
 PIN_TESTS = [
@@ -59,6 +71,11 @@ PIN_TESTS = [
     lambda: pins.test_blend_weights_sum_to_one_and_follow_the_blend_coefficient(),
     lambda: pins.test_blend_larger_RtoL_flow_pulls_weight_towards_L(),
     lambda: pins.test_quantize_u8_rounds_half_to_even_and_clamps(),
+    lambda: [rpins.test_energy_gradient_in_u_matches_central_differences(a) for a in (0.0, 0.05)],
+    lambda: rpins.test_energy_gradients_in_T_and_J_match_central_differences(),
+    lambda: rpins.test_smoothness_energy_closed_form(),
+    lambda: rpins.test_energy_and_gradients_vanish_on_identical_images_and_zero_flow(),
+    lambda: [rpins.test_reduce_transpose_dot_product_identity(s) for s in [(7, 9), (13, 2)]],
 ]
 
 
