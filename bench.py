@@ -8,6 +8,8 @@ both strips, pyramidal LK flow in both directions, and the Code 1 blend
 The metric is overlap megapixels per second.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py --workload rig     # all 8 pairs of a 360-degree rig per step
+  python bench.py --workload refine_1024
 
 With N > 1 (under torchrun) every rank runs its own pair: the pairs are
 independent, there is no data exchange, and the reported value is the pixels
@@ -76,6 +78,37 @@ def path_alg_bytes(h: int, w: int, c: int, levels: int, in_bytes: int = 1):
     flow = sum(lk_alg_bytes(h, w, levels))
     blend = 2 * c * in_bytes * n + 16 * n + c * in_bytes * n
     return pyramid + flow + blend
+
+
+RIG_WORKLOAD = {"workload": "rig_8x4000x{800..2000}_rgb_u8_lv6_canvas_9000x4000", "h": 4000,
+                "widths": [800, 950, 1100, 1250, 1400, 1600, 1800, 2000], "channels": 3, "levels": 6,
+                "iters": 5, "radius": 2, "dmax": 24.0, "canvas": [4000, 9000],
+                "canvas_x0": [1125 * k for k in range(8)]}
+PANO_LK_AUTO, PANO_LK_STREAM, PANO_LK_TILE = 0, 1, 2
+
+
+def rig_level_kernels(h: int, widths, levels: int, kernels):
+    """Kernel launches of each LK level of a rig, in launch order: for level
+    l, [(kernel name, [pairs])] with the streamed batch first. kernels[l] is
+    the level's PANO_LK_* tuning; AUTO uses the single-pair size rule."""
+    out = []
+    for l in range(levels):
+        hl = h
+        ws = list(widths)
+        for _ in range(l):
+            hl = (hl + 1) // 2
+            ws = [(w + 1) // 2 for w in ws]
+        st, ti = [], []
+        for k, w in enumerate(ws):
+            use = kernels[l] == PANO_LK_STREAM or (kernels[l] == PANO_LK_AUTO and hl * w >= STREAM_MIN_PIXELS)
+            (st if use else ti).append(k)
+        lev = []
+        if st:
+            lev.append(("lk_stream_batch_kernel", st))
+        if ti:
+            lev.append(("lk_level_batch_kernel", ti))
+        out.append(lev)
+    return out
 
 
 def throughput(pixels_per_step: int, steps: int, world: int, max_total_ms: float) -> float:
@@ -444,6 +477,201 @@ def run_refine(args):
     return 0
 
 
+def run_rig(args):
+    """The 360-degree rig: 8 RGB u8 pairs of 4000 x {800..2000}, 6 levels,
+    every step one replay of the rig's CUDA graph (luma, REDUCE, batched LK
+    per level, blend into the 9000 x 4000 canvas). The single-pair form
+    (pano_flow_pair + pano_blend_pair per pair) is timed beside it."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import synth
+    import paper_2006_01201_gb300 as pkg
+    from paper_2006_01201_gb300 import binding, build as gpu_build
+
+    gpu_build.build()
+    pkg.load_library()
+    W = RIG_WORKLOAD
+    h, widths, c, levels = W["h"], W["widths"], W["channels"], W["levels"]
+    pairs = synth.rig_pairs(h=h, widths=widths, dmax=W["dmax"], levels=levels, seed0=100 + 8 * rank)
+    params = pkg.Params(levels=levels, iters=W["iters"], radius=W["radius"])
+    rig = binding.Rig(params, h, widths, c=c, dtype=torch.uint8, canvas_hw=tuple(W["canvas"]),
+                      canvas_x0=W["canvas_x0"])
+    Ls = [torch.from_numpy(p.L).to(dev) for p in pairs]
+    Rs = [torch.from_numpy(p.R).to(dev) for p in pairs]
+    canvas = rig.new_canvas(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    npx = h * sum(widths)
+
+    t0 = time.perf_counter()
+    tunings = rig.autotune(Ls, Rs, reps=3, stream=stream) if not args.no_autotune else \
+        [rig.get_tuning(l) for l in range(levels)]
+    tune_s = time.perf_counter() - t0
+
+    def step():
+        rig.run(Ls, Rs, canvas=canvas, use_graph=True, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    sampler.start()
+    launches0 = rig.launches
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    launches = rig.launches - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = reduce_max(sum(step_ms), world)
+    value = throughput(npx, args.steps, world, total_ms)
+
+    # --- eager runs with every launch bracketed by events: per-kernel times
+    rig.trace_enable(0xF, 64 * args.steps)
+    for k in range(args.steps):
+        flush.zero_()
+        rig.run(Ls, Rs, canvas=canvas, use_graph=False, stream=stream)
+    torch.cuda.synchronize()
+    recs = rig.trace_read(64 * args.steps)
+    rig.trace_enable(0, 0)
+    plan = rig_level_kernels(h, widths, levels, [t["kernel"] for t in tunings])
+    names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "rig_blend_kernel"}
+    per_kind, lk_seen = {}, {}
+    stream_bytes = 0.0
+    lk_bytes = [lk_alg_bytes(h, w, levels) for w in widths]
+    for kind, lev, ms in recs:
+        if kind == 4:
+            i = lk_seen.get(lev, 0) % len(plan[lev])
+            lk_seen[lev] = lk_seen.get(lev, 0) + 1
+            name, members = plan[lev][i]
+            if name == "lk_stream_batch_kernel":
+                stream_bytes += sum(lk_bytes[k][lev] for k in members)
+        else:
+            name = names[kind]
+        d = per_kind.setdefault(name, {"launches": 0, "ms": 0.0})
+        d["launches"] += 1
+        d["ms"] += ms
+    traced_total = sum(d["ms"] for d in per_kind.values())
+    for d in per_kind.values():
+        d["share"] = d["ms"] / traced_total if traced_total else None
+        d["ms_per_step"] = d["ms"] / args.steps
+    dominant = max(per_kind, key=lambda k: per_kind[k]["ms"])
+    dk = per_kind[dominant]
+    peak, peak_src = read_peaks()
+    launch_ms = dk["ms"] / dk["launches"]
+    bytes_per_launch = stream_bytes / dk["launches"] if dominant == "lk_stream_batch_kernel" else None
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9 if bytes_per_launch else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None,
+                "traffic": TRAFFIC_PER_LAUNCH.get(dominant), "kernel": dominant,
+                "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
+                "launches_per_step": dk["launches"] / args.steps, "peak_source": f"{peak_src} hbm_gbs"}
+    path_bytes = sum(path_alg_bytes(h, w, c, levels) for w in widths)
+
+    # --- the single-pair form on the same strips: 8 x (flow_pair + blend_pair)
+    ctx = pkg.FlowContext(params, max_h=h, max_w=max(widths), max_c=c)
+    outs = [(torch.empty((h, w, 2), device=dev), torch.empty((h, w, 2), device=dev), torch.empty_like(Ls[k]))
+            for k, w in enumerate(widths)]
+
+    def pair_step():
+        for k in range(len(widths)):
+            ctx.flow_pair(Ls[k], Rs[k], out=outs[k][:2], stream=stream)
+            ctx.blend_pair(Ls[k], Rs[k], outs[k][0], outs[k][1], out=outs[k][2], stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        pair_step()
+    torch.cuda.synchronize()
+    ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev3[k][0].record(stream)
+        pair_step()
+        ev3[k][1].record(stream)
+    torch.cuda.synchronize()
+    pair_ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev3), world)
+    ctx.close()
+
+    # --- end to end: pinned host strips in, the canvas back to pinned host memory
+    Lh = [torch.from_numpy(p.L).pin_memory() for p in pairs]
+    Rh = [torch.from_numpy(p.R).pin_memory() for p in pairs]
+    Ch = torch.empty(tuple(canvas.shape), dtype=canvas.dtype).pin_memory()
+    work = {"L": [torch.empty_like(t) for t in Ls], "R": [torch.empty_like(t) for t in Rs],
+            "canvas": rig.new_canvas(dev)}
+    for _ in range(max(1, args.warmup)):
+        rig.run_host(Lh, Rh, Ch, work, stream=stream)
+    torch.cuda.synchronize()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()
+        ev2[k][0].record(stream)
+        rig.run_host(Lh, Rh, Ch, work, stream=stream)
+        ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    e2e_ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev2), world)
+    e2e = {"value": throughput(npx, args.steps, world, e2e_ms), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(t.numel() for t in Lh + Rh)), "d2h_bytes_per_step": int(Ch.numel()),
+           "ms_per_step": e2e_ms / args.steps}
+
+    line = None
+    if rank == 0:
+        line = {"metric": METRIC.replace("(bi-flow+warp+blend)", "(bi-flow+warp+blend, 8-pair rig)"),
+                "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(W, l2="flushed between steps (256 MB write, untimed); inputs 262 MB > L2",
+                               parallelism=f"replicas{world}", graph=True),
+                "roofline": roofline,
+                "path": {"alg_bytes_per_step": path_bytes,
+                         "achieved_gbs": path_bytes / (total_ms / args.steps * 1e-3) / 1e9},
+                "kernels": per_kind, "dominant_kernel": dominant,
+                "single_pair_form": {"value": throughput(npx, args.steps, world, pair_ms), "unit": UNIT,
+                                     "ms_per_step": pair_ms / args.steps},
+                "autotune": {"seconds": tune_s, "levels": tunings},
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
+        if world == 1 and not args.no_cpu_baseline:
+            import oracle
+            oracle.build()
+            olr, orl = oracle.flow_pair(pairs[0].L, pairs[0].R, oracle.Params(levels=levels))
+            g_lr, g_rl = (t.cpu().numpy() for t in rig.flows(0))
+            line["epe_vs_oracle"] = {
+                "pair": 0,
+                "LtoR_mean_px": float(np.hypot(*(g_lr - olr).transpose(2, 0, 1)).mean()),
+                "RtoL_mean_px": float(np.hypot(*(g_rl - orl).transpose(2, 0, 1)).mean())}
+            v, cores, desc, secs = time_oracle(pairs[0], levels, budget_s=args.cpu_budget)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": desc.replace("of the pair", "of rig pair 0 (4000x800)"),
+                                    "seconds": secs}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    rig.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -452,8 +680,10 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="pair", choices=["pair", "refine_1024"],
-                    help="pair: the 4000x1500 overlap pair (default); refine_1024: the differentiable refinement")
+    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "refine_1024"],
+                    help="pair: the 4000x1500 overlap pair (default); rig: the 8-pair 360-degree rig; "
+                         "refine_1024: the differentiable refinement")
+    ap.add_argument("--no-autotune", action="store_true", help="rig: keep the default tuning")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -461,6 +691,8 @@ def main(argv=None):
         return run_reference(args)
     if args.workload == "refine_1024":
         return run_refine(args)
+    if args.workload == "rig":
+        return run_rig(args)
     return run_gpu(args)
 
 

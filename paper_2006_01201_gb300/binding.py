@@ -1,4 +1,5 @@
-"""ctypes binding of ``libpanoflow.so`` (the C ABI in ``include/pano_flow.h``).
+"""ctypes binding of ``libpanoflow.so`` (the C ABI in ``include/pano_flow.h``
+and ``include/pano_rig.h``).
 
 Argument marshalling only: every step of the path runs in the library's CUDA
 kernels. PyTorch supplies device memory (tensors) and streams. There is no
@@ -47,8 +48,25 @@ class PanoTraceRecord(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("level", ctypes.c_int), ("ms", ctypes.c_float)]
 
 
+RIG_MAX_PAIRS = 8
+PANO_LK_AUTO, PANO_LK_STREAM, PANO_LK_TILE = 0, 1, 2
+
+
+class PanoRigDesc(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int), ("h", ctypes.c_int), ("w", ctypes.c_int * RIG_MAX_PAIRS),
+                ("c", ctypes.c_int), ("dtype", ctypes.c_int), ("canvas_h", ctypes.c_int),
+                ("canvas_w", ctypes.c_int), ("canvas_y0", ctypes.c_int),
+                ("canvas_x0", ctypes.c_int * RIG_MAX_PAIRS)]
+
+
+class PanoRigTuning(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int), ("seg_rows", ctypes.c_int), ("tile_w", ctypes.c_int),
+                ("tile_h", ctypes.c_int), ("ms", ctypes.c_float)]
+
+
 _IMG = ctypes.POINTER(PanoImage)
 _PAR = ctypes.POINTER(PanoParams)
+_PP = ctypes.POINTER(ctypes.c_void_p)
 
 PANO_TRACE_LUMA, PANO_TRACE_PYR_DOWN, PANO_TRACE_LK, PANO_TRACE_BLEND = 0x1, 0x2, 0x4, 0x8
 
@@ -69,6 +87,17 @@ SIGNATURES = {
     "pano_stage_pyr_down": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
     "pano_stage_lk": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _VP], _I),
     "pano_stage_warp": ([_IMG, _VP, _F, _IMG, _VP], _I),
+    "pano_rig_create": ([_PAR, ctypes.POINTER(PanoRigDesc), _PP], _I),
+    "pano_rig_run": ([_VP, _IMG, _IMG, _PP, _PP, _IMG, _I, _VP], _I),
+    "pano_rig_autotune": ([_VP, _IMG, _IMG, _I, _VP], _I),
+    "pano_rig_get_tuning": ([_VP, _I, ctypes.POINTER(PanoRigTuning)], _I),
+    "pano_rig_set_tuning": ([_VP, _I, ctypes.POINTER(PanoRigTuning)], _I),
+    "pano_rig_flows": ([_VP, _I, _PP, _PP], _I),
+    "pano_rig_trace_enable": ([_VP, ctypes.c_uint, _I], _I),
+    "pano_rig_trace_read": ([_VP, ctypes.POINTER(PanoTraceRecord), _I, ctypes.POINTER(ctypes.c_int)], _I),
+    "pano_rig_launches": ([_VP], ctypes.c_ulonglong),
+    "pano_rig_graph_captures": ([_VP], _I),
+    "pano_rig_destroy": ([_VP], _I),
 }
 
 _lib = None
@@ -287,6 +316,159 @@ def flow_pair_static(params: Params, L, R, out=None, stream=None):
                                                 _flow_ptr(out[0], h, w, "flow_LtoR"),
                                                 _flow_ptr(out[1], h, w, "flow_RtoL"), _stream_ptr(stream)))
     return out
+
+
+class Rig:
+    """Every overlap pair of a 360-degree rig per call (``include/pano_rig.h``).
+
+    widths: strip widths of the pairs (all strips are h rows high); strip k
+    lands on canvas columns (canvas_x0[k] + x) mod canvas_w, rows canvas_y0..;
+    where spans overlap, the pair with the higher index writes the canvas.
+    """
+
+    def __init__(self, params: Optional[Params], h: int, widths, c: int = 3, dtype=None,
+                 canvas_hw: Tuple[int, int] = (4000, 9000), canvas_x0=None, canvas_y0: int = 0):
+        torch = _torch()
+        lib = load_library()
+        self.params = params or Params()
+        self.h, self.widths, self.c = h, list(widths), c
+        self.dtype = dtype if dtype is not None else torch.uint8
+        n = len(self.widths)
+        if not 1 <= n <= RIG_MAX_PAIRS:
+            raise PanoError(PANO_ERR_INVALID_ARG, f"{n} pairs (1..{RIG_MAX_PAIRS})")
+        self.canvas_hw = tuple(canvas_hw)
+        self.canvas_x0 = list(canvas_x0) if canvas_x0 is not None else [0] * n
+        self.canvas_y0 = canvas_y0
+        d = PanoRigDesc()
+        d.n_pairs, d.h, d.c = n, h, c
+        d.dtype = PANO_U8 if self.dtype == torch.uint8 else PANO_F32
+        d.canvas_h, d.canvas_w = self.canvas_hw
+        d.canvas_y0 = canvas_y0
+        for k in range(n):
+            d.w[k] = self.widths[k]
+            d.canvas_x0[k] = self.canvas_x0[k]
+        self.desc = d
+        hdl = ctypes.c_void_p()
+        p = self.params.to_c()
+        _check(lib.pano_rig_create(ctypes.byref(p), ctypes.byref(d), ctypes.byref(hdl)))
+        self._h = hdl
+
+    @property
+    def n_pairs(self) -> int:
+        return len(self.widths)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _check(load_library().pano_rig_destroy(self._h))
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _strips(self, Ls, Rs):
+        if len(Ls) != self.n_pairs or len(Rs) != self.n_pairs:
+            raise PanoError(PANO_ERR_INVALID_ARG, f"expected {self.n_pairs} L and R strips")
+        L = (PanoImage * self.n_pairs)(*[image_desc(t) for t in Ls])
+        R = (PanoImage * self.n_pairs)(*[image_desc(t) for t in Rs])
+        return L, R
+
+    def new_canvas(self, device="cuda"):
+        torch = _torch()
+        hc, wc = self.canvas_hw
+        shape = (hc, wc, self.c) if self.c > 1 else (hc, wc)
+        return torch.zeros(shape, dtype=self.dtype, device=device)
+
+    def run(self, Ls, Rs, flows=None, canvas=None, use_graph: bool = False, stream=None):
+        """Flows of every pair (list of (FlowLtoR, FlowRtoL) tensors, or None to keep
+        them in the rig) and, with a canvas tensor, the blended strips placed on it."""
+        L, R = self._strips(Ls, Rs)
+        lr = rl = None
+        if flows is not None:
+            if len(flows) != self.n_pairs:
+                raise PanoError(PANO_ERR_INVALID_ARG, f"expected {self.n_pairs} flow pairs")
+            lr = (ctypes.c_void_p * self.n_pairs)(*[_flow_ptr(f[0], self.h, w, "flow_LtoR")
+                                                     for f, w in zip(flows, self.widths)])
+            rl = (ctypes.c_void_p * self.n_pairs)(*[_flow_ptr(f[1], self.h, w, "flow_RtoL")
+                                                     for f, w in zip(flows, self.widths)])
+        dc = ctypes.byref(image_desc(canvas)) if canvas is not None else None
+        _check(load_library().pano_rig_run(self._h, L, R, lr, rl, dc, int(bool(use_graph)), _stream_ptr(stream)))
+        return canvas
+
+    def run_host(self, L_host, R_host, canvas_host, work, use_graph: bool = True, stream=None):
+        """Whole rig from host strips to a host canvas on one stream: H2D copies of
+        every strip into ``work["L"]``/``work["R"]`` (lists of device tensors), the
+        rig run into ``work["canvas"]`` and the D2H copy of the canvas. Returns
+        without synchronising."""
+        torch = _torch()
+        s = stream if stream is not None else torch.cuda.current_stream()
+        with torch.cuda.stream(s):
+            for dst, src in zip(work["L"], L_host):
+                dst.copy_(src, non_blocking=True)
+            for dst, src in zip(work["R"], R_host):
+                dst.copy_(src, non_blocking=True)
+            self.run(work["L"], work["R"], canvas=work["canvas"], use_graph=use_graph, stream=s)
+            canvas_host.copy_(work["canvas"], non_blocking=True)
+        return canvas_host
+
+    def flows(self, k: int, copy: bool = True):
+        """(FlowLtoR, FlowRtoL) of pair k kept in the rig: copies, or (copy=False)
+        views of the rig's buffers, valid while the rig lives."""
+        torch = _torch()
+        a, b = ctypes.c_void_p(), ctypes.c_void_p()
+        _check(load_library().pano_rig_flows(self._h, k, ctypes.byref(a), ctypes.byref(b)))
+        shape = (self.h, self.widths[k], 2)
+        out = tuple(torch.as_tensor(_DeviceArray(ptr, shape), device="cuda") for ptr in (a.value, b.value))
+        return tuple(t.clone() for t in out) if copy else out
+
+    def autotune(self, Ls, Rs, reps: int = 5, stream=None):
+        L, R = self._strips(Ls, Rs)
+        _check(load_library().pano_rig_autotune(self._h, L, R, reps, _stream_ptr(stream)))
+        return [self.get_tuning(l) for l in range(self.params.levels)]
+
+    def get_tuning(self, level: int) -> dict:
+        t = PanoRigTuning()
+        _check(load_library().pano_rig_get_tuning(self._h, level, ctypes.byref(t)))
+        return {"kernel": t.kernel, "seg_rows": t.seg_rows, "tile_w": t.tile_w, "tile_h": t.tile_h, "ms": t.ms}
+
+    def set_tuning(self, level: int, kernel: int = PANO_LK_AUTO, seg_rows: int = 0, tile_w: int = 0,
+                   tile_h: int = 0) -> None:
+        t = PanoRigTuning(kernel, seg_rows, tile_w, tile_h, 0.0)
+        _check(load_library().pano_rig_set_tuning(self._h, level, ctypes.byref(t)))
+
+    def trace_enable(self, kind_mask: int, capacity: int) -> None:
+        _check(load_library().pano_rig_trace_enable(self._h, kind_mask, capacity))
+
+    def trace_read(self, max_records: int = 4096):
+        buf = (PanoTraceRecord * max_records)()
+        n = ctypes.c_int()
+        _check(load_library().pano_rig_trace_read(self._h, buf, max_records, ctypes.byref(n)))
+        return [(buf[i].kind, buf[i].level, buf[i].ms) for i in range(n.value)]
+
+    @property
+    def launches(self) -> int:
+        return int(load_library().pano_rig_launches(self._h))
+
+    @property
+    def graph_captures(self) -> int:
+        return int(load_library().pano_rig_graph_captures(self._h))
+
+
+class _DeviceArray:
+    """A float32 device buffer of the library, exposed through the CUDA array
+    interface so that torch can view it without a copy."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
 
 
 # ---------------------------------------------------------------------------

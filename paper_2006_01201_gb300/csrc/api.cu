@@ -17,30 +17,13 @@
 
 using namespace pano;
 
-struct pano_flow_ctx {
-    pano_flow_params p;
-    int max_h, max_w, max_c;
-    int device;
-    int nlev;
-    int lev_h[kMaxLevels], lev_w[kMaxLevels];  // level sizes at the maximum strip size
-    int lev_pitch[kMaxLevels];                 // floats
-    int flow_pitch[kMaxLevels];                // float2 elements
-    float* pyr[2][kMaxLevels];                 // luma pyramids of L and R
-    float* flw[2][kMaxLevels];                 // flows of levels >= 1, per direction
-    void* buf;
-    size_t buf_bytes;
-    int tile_w, tile_h;
-    unsigned long long launches;
-    // tracing
-    unsigned trace_mask;
-    int trace_cap, trace_n;
-    cudaEvent_t* ev;  // 2 * trace_cap events: start, stop per record
-    pano_trace_record* rec;
-};
+#include "ctx.h"
 
 namespace {
-
 thread_local char g_err[512] = "";
+}  // namespace
+
+namespace pano {
 
 pano_status fail(pano_status st, const char* fmt, ...) {
     va_list ap;
@@ -146,32 +129,72 @@ pano_status ensure_lk_ready(int* max_smem_out) {
     return PANO_OK;
 }
 
-void trace_free(pano_flow_ctx* c) {
-    if (c->ev) {
-        for (int i = 0; i < 2 * c->trace_cap; ++i)
-            if (c->ev[i]) cudaEventDestroy(c->ev[i]);
-        delete[] c->ev;
+void trace_free(Trace& t) {
+    if (t.ev) {
+        for (int i = 0; i < 2 * t.cap; ++i)
+            if (t.ev[i]) cudaEventDestroy(t.ev[i]);
+        delete[] t.ev;
     }
-    delete[] c->rec;
-    c->ev = nullptr;
-    c->rec = nullptr;
-    c->trace_cap = c->trace_n = 0;
-    c->trace_mask = 0;
+    delete[] t.rec;
+    t.ev = nullptr;
+    t.rec = nullptr;
+    t.cap = t.n = 0;
+    t.mask = 0;
 }
 
-// Brackets one launch with events when its kind is traced; returns the slot.
-int trace_begin(pano_flow_ctx* c, unsigned kind, int level, cudaStream_t s) {
-    if (!(c->trace_mask & kind) || c->trace_n >= c->trace_cap) return -1;
-    int i = c->trace_n++;
-    c->rec[i].kind = (int)kind;
-    c->rec[i].level = level;
-    c->rec[i].ms = 0.f;
-    cudaEventRecord(c->ev[2 * i], s);
+int trace_begin(Trace& t, unsigned kind, int level, cudaStream_t s) {
+    if (!(t.mask & kind) || t.n >= t.cap) return -1;
+    int i = t.n++;
+    t.rec[i].kind = (int)kind;
+    t.rec[i].level = level;
+    t.rec[i].ms = 0.f;
+    cudaEventRecord(t.ev[2 * i], s);
     return i;
 }
 
-void trace_end(pano_flow_ctx* c, int slot, cudaStream_t s) {
-    if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], s);
+void trace_end(Trace& t, int slot, cudaStream_t s) {
+    if (slot >= 0) cudaEventRecord(t.ev[2 * slot + 1], s);
+}
+
+pano_status trace_enable(Trace& t, unsigned kind_mask, int capacity) {
+    if (capacity < 0 || capacity > (1 << 20)) return fail(PANO_ERR_INVALID_ARG, "capacity %d", capacity);
+    trace_free(t);
+    if (capacity == 0 || kind_mask == 0) return PANO_OK;
+    t.ev = new (std::nothrow) cudaEvent_t[2 * (size_t)capacity]();
+    t.rec = new (std::nothrow) pano_trace_record[capacity];
+    if (!t.ev || !t.rec) {
+        delete[] t.ev;
+        delete[] t.rec;
+        t.ev = nullptr;
+        t.rec = nullptr;
+        return fail(PANO_ERR_OOM, "host allocation failed");
+    }
+    t.cap = capacity;
+    for (int i = 0; i < 2 * capacity; ++i) {
+        cudaError_t e = cudaEventCreate(&t.ev[i]);
+        if (e != cudaSuccess) {
+            trace_free(t);
+            return cuda_fail(e, "cudaEventCreate");
+        }
+    }
+    t.mask = kind_mask;
+    t.n = 0;
+    return PANO_OK;
+}
+
+pano_status trace_read(Trace& t, pano_trace_record* out, int max_records, int* n_out) {
+    if (!n_out || (max_records > 0 && !out)) return fail(PANO_ERR_INVALID_ARG, "NULL argument");
+    *n_out = 0;
+    int n = t.n < max_records ? t.n : max_records;
+    for (int i = 0; i < n; ++i) {
+        cudaError_t e = cudaEventSynchronize(t.ev[2 * i + 1]);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&t.rec[i].ms, t.ev[2 * i], t.ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "reading trace events");
+        out[i] = t.rec[i];
+    }
+    *n_out = n;
+    t.n = 0;
+    return PANO_OK;
 }
 
 ImageDesc desc(const pano_image* im) {
@@ -185,9 +208,111 @@ ImageDesc desc(const pano_image* im) {
     return d;
 }
 
-}  // namespace
+void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
 
-void pano::set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
+pano_status check_pair_call(const pano_flow_ctx* c, const pano_image* L, const pano_image* R, const float* lr,
+                            const float* rl) {
+    if (!c) return fail(PANO_ERR_INVALID_ARG, "context is NULL");
+    pano_status st;
+    if ((st = check_image(L, "L")) != PANO_OK) return st;
+    if ((st = check_image(R, "R")) != PANO_OK) return st;
+    if ((st = check_same(L, R, "L", "R")) != PANO_OK) return st;
+    if ((st = check_flow(lr, "flow_LtoR")) != PANO_OK) return st;
+    if ((st = check_flow(rl, "flow_RtoL")) != PANO_OK) return st;
+    if (L->h > c->max_h || L->w > c->max_w || L->c > c->max_c)
+        return fail(PANO_ERR_INVALID_ARG, "strip %dx%dx%d exceeds the context maximum %dx%dx%d", L->h, L->w,
+                    L->c, c->max_h, c->max_w, c->max_c);
+    const size_t fbytes = (size_t)L->h * L->w * 2 * sizeof(float);
+    if (overlaps(lr, fbytes, rl, fbytes)) return fail(PANO_ERR_INVALID_ARG, "the two flows overlap");
+    return PANO_OK;
+}
+
+void pair_planes(const pano_flow_ctx* c, const pano_image* L, const pano_image* R, PairPlanes* pp) {
+    memset(pp, 0, sizeof(*pp));
+    const int nlev = c->nlev;
+    pp->hs[0] = L->h;
+    pp->ws[0] = L->w;
+    for (int l = 1; l < nlev; ++l) {
+        pp->hs[l] = (pp->hs[l - 1] + 1) / 2;
+        pp->ws[l] = (pp->ws[l - 1] + 1) / 2;
+    }
+    const pano_image* img[2] = {L, R};
+    for (int si = 0; si < 2; ++si) {
+        for (int l = 0; l < nlev; ++l) {
+            pp->plane[si][l] = c->pyr[si][l];
+            pp->pitch[si][l] = c->lev_pitch[l];
+        }
+        if (img[si]->dtype == PANO_F32 && img[si]->c == 1) {
+            // a one-channel float strip is its own luma
+            pp->plane[si][0] = static_cast<const float*>(img[si]->data);
+            pp->pitch[si][0] = (int)(img[si]->pitch_bytes / sizeof(float));
+        } else {
+            LumaArgs& la = pp->luma;
+            la.in[la.count] = desc(img[si]);
+            la.out[la.count] = c->pyr[si][0];
+            la.out_pitch[la.count] = c->lev_pitch[0];
+            la.count++;
+        }
+    }
+}
+
+cudaError_t launch_pair_pyramid(pano_flow_ctx* c, const PairPlanes& pp, cudaStream_t s) {
+    cudaError_t e;
+    if (pp.luma.count > 0) {
+        int t = trace_begin(c->tr, PANO_TRACE_LUMA, 0, s);
+        if ((e = launch_luma(pp.luma, s)) != cudaSuccess) return e;
+        trace_end(c->tr, t, s);
+        c->launches++;
+    }
+    for (int l = 1; l < c->nlev; ++l) {
+        PyrDownArgs pa;
+        memset(&pa, 0, sizeof(pa));
+        for (int si = 0; si < 2; ++si) {
+            pa.src[si] = pp.plane[si][l - 1];
+            pa.src_pitch[si] = pp.pitch[si][l - 1];
+            pa.dst[si] = c->pyr[si][l];
+            pa.dst_pitch[si] = c->lev_pitch[l];
+        }
+        pa.h[0] = pa.h[1] = pp.hs[l - 1];
+        pa.w[0] = pa.w[1] = pp.ws[l - 1];
+        pa.count = 2;
+        int t = trace_begin(c->tr, PANO_TRACE_PYR_DOWN, l, s);
+        if ((e = launch_pyr_down(pa, s)) != cudaSuccess) return e;
+        trace_end(c->tr, t, s);
+        c->launches++;
+    }
+    return cudaSuccess;
+}
+
+void pair_lk_args(const pano_flow_ctx* c, const PairPlanes& pp, int l, float* flow_LtoR, float* flow_RtoL,
+                  LkArgs* ka) {
+    const int nlev = c->nlev;
+    float* out[2] = {flow_LtoR, flow_RtoL};
+    memset(ka, 0, sizeof(*ka));
+    for (int d = 0; d < 2; ++d) {
+        // direction 0: FlowLtoR (template L, target R); 1: FlowRtoL
+        ka->dir[d].T = pp.plane[d][l];
+        ka->dir[d].pitchT = pp.pitch[d][l];
+        ka->dir[d].J = pp.plane[1 - d][l];
+        ka->dir[d].pitchJ = pp.pitch[1 - d][l];
+        ka->dir[d].uin = l == nlev - 1 ? nullptr : c->flw[d][l + 1];
+        ka->dir[d].uin_pitch = l == nlev - 1 ? 0 : c->flow_pitch[l + 1];
+        ka->dir[d].uout = l == 0 ? out[d] : c->flw[d][l];
+        ka->dir[d].uout_pitch = l == 0 ? pp.ws[0] : c->flow_pitch[l];
+    }
+    ka->h = pp.hs[l];
+    ka->w = pp.ws[l];
+    ka->in_h = l == nlev - 1 ? 0 : pp.hs[l + 1];
+    ka->in_w = l == nlev - 1 ? 0 : pp.ws[l + 1];
+    ka->mode = l == nlev - 1 ? 0 : 1;
+    ka->iters = c->p.iters;
+    ka->radius = c->p.radius;
+    ka->lambda = c->p.lambda;
+    ka->tile_w = c->tile_w;
+    ka->tile_h = c->tile_h;
+}
+
+}  // namespace pano
 
 extern "C" {
 
@@ -268,7 +393,7 @@ pano_status pano_flow_create(const pano_flow_params* p, int max_h, int max_w, in
 
 pano_status pano_flow_destroy(pano_flow_ctx* c) {
     if (!c) return PANO_OK;
-    trace_free(c);
+    trace_free(c->tr);
     cudaError_t e = c->buf ? cudaFree(c->buf) : cudaSuccess;
     delete c;
     if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
@@ -277,100 +402,19 @@ pano_status pano_flow_destroy(pano_flow_ctx* c) {
 
 pano_status pano_flow_pair(pano_flow_ctx* c, const pano_image* L, const pano_image* R,
                            float* flow_LtoR, float* flow_RtoL, void* cuda_stream) {
-    if (!c) return fail(PANO_ERR_INVALID_ARG, "context is NULL");
-    pano_status st;
-    if ((st = check_image(L, "L")) != PANO_OK) return st;
-    if ((st = check_image(R, "R")) != PANO_OK) return st;
-    if ((st = check_same(L, R, "L", "R")) != PANO_OK) return st;
-    if ((st = check_flow(flow_LtoR, "flow_LtoR")) != PANO_OK) return st;
-    if ((st = check_flow(flow_RtoL, "flow_RtoL")) != PANO_OK) return st;
-    if (L->h > c->max_h || L->w > c->max_w || L->c > c->max_c)
-        return fail(PANO_ERR_INVALID_ARG, "strip %dx%dx%d exceeds the context maximum %dx%dx%d", L->h, L->w,
-                    L->c, c->max_h, c->max_w, c->max_c);
-    const size_t fbytes = (size_t)L->h * L->w * 2 * sizeof(float);
-    if (overlaps(flow_LtoR, fbytes, flow_RtoL, fbytes)) return fail(PANO_ERR_INVALID_ARG, "the two flows overlap");
+    pano_status st = check_pair_call(c, L, R, flow_LtoR, flow_RtoL);
+    if (st != PANO_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    const int nlev = c->nlev;
-    int hs[kMaxLevels], ws[kMaxLevels];
-    hs[0] = L->h;
-    ws[0] = L->w;
-    for (int l = 1; l < nlev; ++l) {
-        hs[l] = (hs[l - 1] + 1) / 2;
-        ws[l] = (ws[l - 1] + 1) / 2;
-    }
-    // Level-0 planes: a one-channel float strip is its own luma.
-    const float* plane[2][kMaxLevels];
-    int ppitch[2][kMaxLevels];
-    const pano_image* img[2] = {L, R};
-    LumaArgs la;
-    memset(&la, 0, sizeof(la));
-    for (int si = 0; si < 2; ++si) {
-        for (int l = 0; l < nlev; ++l) {
-            plane[si][l] = c->pyr[si][l];
-            ppitch[si][l] = c->lev_pitch[l];
-        }
-        if (img[si]->dtype == PANO_F32 && img[si]->c == 1) {
-            plane[si][0] = static_cast<const float*>(img[si]->data);
-            ppitch[si][0] = (int)(img[si]->pitch_bytes / sizeof(float));
-        } else {
-            la.in[la.count] = desc(img[si]);
-            la.out[la.count] = c->pyr[si][0];
-            la.out_pitch[la.count] = c->lev_pitch[0];
-            la.count++;
-        }
-    }
+    PairPlanes pp;
+    pair_planes(c, L, R, &pp);
     cudaError_t e;
-    if (la.count > 0) {
-        int t = trace_begin(c, PANO_TRACE_LUMA, 0, s);
-        if ((e = launch_luma(la, s)) != cudaSuccess) return cuda_fail(e, "luma launch");
-        trace_end(c, t, s);
-        c->launches++;
-    }
-    for (int l = 1; l < nlev; ++l) {
-        PyrDownArgs pa;
-        memset(&pa, 0, sizeof(pa));
-        for (int si = 0; si < 2; ++si) {
-            pa.src[si] = plane[si][l - 1];
-            pa.src_pitch[si] = ppitch[si][l - 1];
-            pa.dst[si] = c->pyr[si][l];
-            pa.dst_pitch[si] = c->lev_pitch[l];
-        }
-        pa.h = hs[l - 1];
-        pa.w = ws[l - 1];
-        pa.count = 2;
-        int t = trace_begin(c, PANO_TRACE_PYR_DOWN, l, s);
-        if ((e = launch_pyr_down(pa, s)) != cudaSuccess) return cuda_fail(e, "pyramid launch");
-        trace_end(c, t, s);
-        c->launches++;
-    }
-    float* out[2] = {flow_LtoR, flow_RtoL};
-    for (int l = nlev - 1; l >= 0; --l) {
+    if ((e = launch_pair_pyramid(c, pp, s)) != cudaSuccess) return cuda_fail(e, "pyramid launch");
+    for (int l = c->nlev - 1; l >= 0; --l) {
         LkArgs ka;
-        memset(&ka, 0, sizeof(ka));
-        for (int d = 0; d < 2; ++d) {
-            // direction 0: FlowLtoR (template L, target R); 1: FlowRtoL
-            ka.dir[d].T = plane[d][l];
-            ka.dir[d].pitchT = ppitch[d][l];
-            ka.dir[d].J = plane[1 - d][l];
-            ka.dir[d].pitchJ = ppitch[1 - d][l];
-            ka.dir[d].uin = l == nlev - 1 ? nullptr : c->flw[d][l + 1];
-            ka.dir[d].uin_pitch = l == nlev - 1 ? 0 : c->flow_pitch[l + 1];
-            ka.dir[d].uout = l == 0 ? out[d] : c->flw[d][l];
-            ka.dir[d].uout_pitch = l == 0 ? ws[0] : c->flow_pitch[l];
-        }
-        ka.h = hs[l];
-        ka.w = ws[l];
-        ka.in_h = l == nlev - 1 ? 0 : hs[l + 1];
-        ka.in_w = l == nlev - 1 ? 0 : ws[l + 1];
-        ka.mode = l == nlev - 1 ? 0 : 1;
-        ka.iters = c->p.iters;
-        ka.radius = c->p.radius;
-        ka.lambda = c->p.lambda;
-        ka.tile_w = c->tile_w;
-        ka.tile_h = c->tile_h;
-        int t = trace_begin(c, PANO_TRACE_LK, l, s);
+        pair_lk_args(c, pp, l, flow_LtoR, flow_RtoL, &ka);
+        int t = trace_begin(c->tr, PANO_TRACE_LK, l, s);
         if ((e = launch_lk_level(ka, 2, s)) != cudaSuccess) return cuda_fail(e, "LK launch");
-        trace_end(c, t, s);
+        trace_end(c->tr, t, s);
         c->launches++;
     }
     return PANO_OK;
@@ -404,54 +448,22 @@ pano_status pano_blend_pair(pano_flow_ctx* c, const pano_image* L, const pano_im
     a.k_sharp = c->p.soft_sharpness;
     a.k_mag = c->p.flow_mag_coef;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    int t = trace_begin(c, PANO_TRACE_BLEND, 0, s);
+    int t = trace_begin(c->tr, PANO_TRACE_BLEND, 0, s);
     cudaError_t e = launch_blend(a, s);
     if (e != cudaSuccess) return cuda_fail(e, "blend launch");
-    trace_end(c, t, s);
+    trace_end(c->tr, t, s);
     c->launches++;
     return PANO_OK;
 }
 
 pano_status pano_trace_enable(pano_flow_ctx* c, unsigned kind_mask, int capacity) {
     if (!c) return fail(PANO_ERR_INVALID_ARG, "context is NULL");
-    if (capacity < 0 || capacity > (1 << 20)) return fail(PANO_ERR_INVALID_ARG, "capacity %d", capacity);
-    trace_free(c);
-    if (capacity == 0 || kind_mask == 0) return PANO_OK;
-    c->ev = new (std::nothrow) cudaEvent_t[2 * (size_t)capacity]();
-    c->rec = new (std::nothrow) pano_trace_record[capacity];
-    if (!c->ev || !c->rec) {
-        delete[] c->ev;
-        delete[] c->rec;
-        c->ev = nullptr;
-        c->rec = nullptr;
-        return fail(PANO_ERR_OOM, "host allocation failed");
-    }
-    c->trace_cap = capacity;
-    for (int i = 0; i < 2 * capacity; ++i) {
-        cudaError_t e = cudaEventCreate(&c->ev[i]);
-        if (e != cudaSuccess) {
-            trace_free(c);
-            return cuda_fail(e, "cudaEventCreate");
-        }
-    }
-    c->trace_mask = kind_mask;
-    c->trace_n = 0;
-    return PANO_OK;
+    return trace_enable(c->tr, kind_mask, capacity);
 }
 
 pano_status pano_trace_read(pano_flow_ctx* c, pano_trace_record* out, int max_records, int* n_out) {
-    if (!c || !n_out || (max_records > 0 && !out)) return fail(PANO_ERR_INVALID_ARG, "NULL argument");
-    *n_out = 0;
-    int n = c->trace_n < max_records ? c->trace_n : max_records;
-    for (int i = 0; i < n; ++i) {
-        cudaError_t e = cudaEventSynchronize(c->ev[2 * i + 1]);
-        if (e == cudaSuccess) e = cudaEventElapsedTime(&c->rec[i].ms, c->ev[2 * i], c->ev[2 * i + 1]);
-        if (e != cudaSuccess) return cuda_fail(e, "reading trace events");
-        out[i] = c->rec[i];
-    }
-    *n_out = n;
-    c->trace_n = 0;
-    return PANO_OK;
+    if (!c) return fail(PANO_ERR_INVALID_ARG, "NULL argument");
+    return trace_read(c->tr, out, max_records, n_out);
 }
 
 unsigned long long pano_flow_launches(const pano_flow_ctx* c) { return c ? c->launches : 0ull; }
@@ -487,8 +499,8 @@ pano_status pano_stage_pyr_down(const float* src, int h, int w, int src_pitch, f
     pa.dst[0] = dst;
     pa.src_pitch[0] = src_pitch;
     pa.dst_pitch[0] = dst_pitch;
-    pa.h = h;
-    pa.w = w;
+    pa.h[0] = h;
+    pa.w[0] = w;
     pa.count = 1;
     cudaError_t e = launch_pyr_down(pa, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? PANO_OK : cuda_fail(e, "pyramid launch");

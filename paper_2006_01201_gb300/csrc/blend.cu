@@ -24,8 +24,9 @@ __device__ __forceinline__ float sample_channel(const Tv* __restrict__ base, con
                         (float)base[t.o11 + k]);
 }
 
+// F at strip pixel (x, y), stored at column `fx` of row y of a.F.
 template <typename Tv, int C>
-__device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y) {
+__device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y, int fx) {
     const int w = a.L.w, h = a.L.h;
     const long long p = (long long)y * w + x;
     const float B = a.blend ? a.blend[p] : (float)(x + 1) / (float)(w + 1);
@@ -44,7 +45,7 @@ __device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y) {
     const float wR = e * wL;
     const Tv* __restrict__ Lb = static_cast<const Tv*>(a.L.data);
     const Tv* __restrict__ Rb = static_cast<const Tv*>(a.R.data);
-    Tv* out = reinterpret_cast<Tv*>(static_cast<char*>(a.F) + (long long)y * a.F_pitch_bytes) + x * C;
+    Tv* out = reinterpret_cast<Tv*>(static_cast<char*>(a.F) + (long long)y * a.F_pitch_bytes) + (long long)fx * C;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         const float cl = sample_channel(Lb, tl, k);
@@ -63,7 +64,30 @@ __global__ void __launch_bounds__(256) blend_kernel(BlendArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.L.w || y >= a.L.h) return;
-    blend_pixel<Tv, C>(a, x, y);
+    blend_pixel<Tv, C>(a, x, y, x);
+}
+
+// Every pair of a rig blended straight into the panorama canvas (Code 1's
+// final placement of Area3): strip column x of pair p lands on canvas column
+// (x0[p] + x) mod canvas_w. Where the spans of several pairs cover a canvas
+// column, the pair with the highest index owns it; the others skip it, so
+// every canvas pixel has one writer and the result is deterministic.
+template <typename Tv, int C>
+__global__ void __launch_bounds__(256) rig_blend_kernel(const __grid_constant__ RigBlendArgs r) {
+    const int p = blockIdx.z;
+    const BlendArgs& a = r.pair[p];
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= a.L.w || y >= a.L.h) return;
+    const int W = r.canvas_w;
+    int cx = r.x0[p] + x;
+    if (cx >= W) cx -= W;
+    for (int q = p + 1; q < r.n; ++q) {
+        int d = cx - r.x0[q];
+        if (d < 0) d += W;
+        if (d < r.pair[q].L.w) return;
+    }
+    blend_pixel<Tv, C>(a, x, y, cx);
 }
 
 template <typename Tv>
@@ -92,6 +116,26 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     } else {
         if (a.L.c == 3) blend_kernel<float, 3><<<grid, block, 0, s>>>(a);
         else blend_kernel<float, 1><<<grid, block, 0, s>>>(a);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rig_blend(const RigBlendArgs& r, cudaStream_t s) {
+    if (r.n < 1 || r.n > kMaxBatch) return cudaErrorInvalidValue;
+    int h = 0, w = 0;
+    for (int p = 0; p < r.n; ++p) {
+        h = max(h, r.pair[p].L.h);
+        w = max(w, r.pair[p].L.w);
+    }
+    dim3 block(32, 8);
+    dim3 grid((w + 31) / 32, (h + 7) / 8, r.n);
+    const ImageDesc& d = r.pair[0].L;
+    if (d.dtype == 0) {
+        if (d.c == 3) rig_blend_kernel<uint8_t, 3><<<grid, block, 0, s>>>(r);
+        else rig_blend_kernel<uint8_t, 1><<<grid, block, 0, s>>>(r);
+    } else {
+        if (d.c == 3) rig_blend_kernel<float, 3><<<grid, block, 0, s>>>(r);
+        else rig_blend_kernel<float, 1><<<grid, block, 0, s>>>(r);
     }
     return cudaGetLastError();
 }

@@ -71,20 +71,26 @@ struct ImageDesc {
     int dtype;  // 0 = u8, 1 = f32
 };
 
-// Level-0 luma of up to two images in one launch (blockIdx.z selects one).
+// Strip pairs in one batched launch, and the planes (two per pair) they hold.
+constexpr int kMaxBatch = 8;
+constexpr int kMaxPlanes = 2 * kMaxBatch;
+
+// Level-0 luma of up to kMaxPlanes images in one launch (blockIdx.z selects
+// one; kernels take the descriptor as a __grid_constant__ parameter and index
+// it in place).
 struct LumaArgs {
-    ImageDesc in[2];
-    float* out[2];
-    int out_pitch[2];
+    ImageDesc in[kMaxPlanes];
+    float* out[kMaxPlanes];
+    int out_pitch[kMaxPlanes];
     int count;
 };
 
-// One REDUCE step of up to two planes in one launch.
+// One REDUCE step of up to kMaxPlanes planes of any sizes in one launch.
 struct PyrDownArgs {
-    const float* src[2];
-    float* dst[2];
-    int src_pitch[2], dst_pitch[2];
-    int h, w;  // source size
+    const float* src[kMaxPlanes];
+    float* dst[kMaxPlanes];
+    int src_pitch[kMaxPlanes], dst_pitch[kMaxPlanes];
+    int h[kMaxPlanes], w[kMaxPlanes];  // source sizes
     int count;
 };
 
@@ -106,7 +112,19 @@ struct LkArgs {
     int mode;            // 0 zero start, 1 upsample coarse uin, 2 uin as is
     int iters, radius;
     float lambda;
-    int tile_w, tile_h;
+    int tile_w, tile_h;  // tiled kernel
+    int seg_rows;        // streamed kernel: segment height (0 = automatic)
+};
+
+// The same pyramid level of several strip pairs in one launch (all share
+// iters and radius): persistent for the streamed kernel, one grid over every
+// pair and direction for the tiled one (all pairs then share the tile shape).
+struct LkBatch {
+    LkArgs pair[kMaxBatch];
+    int n;
+    int nb[kMaxBatch], seg[kMaxBatch], nseg[kMaxBatch];  // filled by the launcher
+    int start[kMaxBatch + 1];                             // item prefix sums
+    unsigned* counter;                                    // device work counter
 };
 
 // Code 1 blend or the plain flow warp.
@@ -118,6 +136,15 @@ struct BlendArgs {
     void* F;
     long long F_pitch_bytes;
     float k_sharp, k_mag;
+};
+
+// Blend of every pair of a rig into one canvas (F of each pair is the canvas
+// row of strip row 0; the column comes from x0).
+struct RigBlendArgs {
+    BlendArgs pair[kMaxBatch];
+    int x0[kMaxBatch];  // canvas column of strip column 0, in [0, canvas_w)
+    int n;
+    int canvas_w;
 };
 
 struct WarpArgs {
@@ -149,13 +176,16 @@ cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s);
 constexpr long long kStreamMinPixels = 100000;
 cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s);
 cudaError_t launch_lk_tile(const LkArgs& a, int ndirs, cudaStream_t s);
+cudaError_t launch_lk_tile_batch(const LkBatch& b, cudaStream_t s);
 // Streamed form of the same level (lk_stream.cu), used for 1 <= iters <= 5.
 bool lk_stream_supports(int iters, int radius);
 cudaError_t lk_stream_prepare(int max_smem_bytes);
 cudaError_t launch_lk_stream(const LkArgs& a, int ndirs, cudaStream_t s);
+cudaError_t launch_lk_stream_batch(const LkBatch& b, int n_ctas, cudaStream_t s);
 size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius);
 cudaError_t lk_prepare(int max_smem_bytes);
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
+cudaError_t launch_rig_blend(const RigBlendArgs& r, cudaStream_t s);
 cudaError_t launch_warp(const WarpArgs& a, cudaStream_t s);
 
 cudaError_t launch_energy_grad(const EnergyArgs& a, cudaStream_t s);

@@ -1,0 +1,80 @@
+// ctx.h -- internal: the flow context of the C ABI and the steps of
+// pano_flow_pair that the multi-pair rig reuses. Not a public header.
+#pragma once
+
+#include "common.cuh"
+#include "pano_flow.h"
+
+namespace pano {
+
+// Launch tracing of one context: events around selected launches.
+struct Trace {
+    unsigned mask;
+    int cap, n;
+    cudaEvent_t* ev;        // 2 * cap events: start, stop per record
+    pano_trace_record* rec;
+};
+
+}  // namespace pano
+
+struct pano_flow_ctx {
+    pano_flow_params p;
+    int max_h, max_w, max_c;
+    int device;
+    int nlev;
+    int lev_h[pano::kMaxLevels], lev_w[pano::kMaxLevels];  // level sizes at the maximum strip size
+    int lev_pitch[pano::kMaxLevels];                 // floats
+    int flow_pitch[pano::kMaxLevels];                // float2 elements
+    float* pyr[2][pano::kMaxLevels];                 // luma pyramids of L and R
+    float* flw[2][pano::kMaxLevels];                 // flows of levels >= 1, per direction
+    void* buf;
+    size_t buf_bytes;
+    int tile_w, tile_h;
+    unsigned long long launches;
+    pano::Trace tr;
+};
+
+namespace pano {
+
+// Plane pointers and pitches of every pyramid level of both strips of one
+// call (level 0 of a one-channel float strip is the strip itself).
+struct PairPlanes {
+    const float* plane[2][kMaxLevels];
+    int pitch[2][kMaxLevels];
+    int hs[kMaxLevels], ws[kMaxLevels];
+    LumaArgs luma;  // level-0 conversions needed (count may be 0)
+};
+
+void pair_planes(const pano_flow_ctx* c, const pano_image* L, const pano_image* R, PairPlanes* pp);
+// luma + REDUCE launches of one pair; returns the first launch error
+cudaError_t launch_pair_pyramid(pano_flow_ctx* c, const PairPlanes& pp, cudaStream_t s);
+// arguments of LK level l of one pair (both directions)
+void pair_lk_args(const pano_flow_ctx* c, const PairPlanes& pp, int l, float* flow_LtoR, float* flow_RtoL,
+                  LkArgs* ka);
+pano_status check_pair_call(const pano_flow_ctx* c, const pano_image* L, const pano_image* R, const float* lr,
+                            const float* rl);
+
+// Argument checks and error reporting shared by the C entry points: each
+// failing check stores its message for pano_last_error and returns the
+// status.
+pano_status fail(pano_status st, const char* fmt, ...);
+pano_status cuda_fail(cudaError_t e, const char* what);
+pano_status check_image(const pano_image* im, const char* name);
+pano_status check_same(const pano_image* a, const pano_image* b, const char* na, const char* nb);
+pano_status check_flow(const void* f, const char* name);
+pano_status check_params(const pano_flow_params* p);
+bool overlaps(const void* a, size_t na, const void* b, size_t nb);
+size_t align_up(size_t v, size_t a);
+ImageDesc desc(const pano_image* im);
+// largest tile of the LK tile kernel that fits max_smem bytes
+bool pick_tile(int iters, int radius, int max_smem, int* tw, int* th);
+// sets the kernels' shared-memory limits once per device; returns the limit
+pano_status ensure_lk_ready(int* max_smem_out);
+
+void trace_free(Trace& t);
+pano_status trace_enable(Trace& t, unsigned kind_mask, int capacity);
+pano_status trace_read(Trace& t, pano_trace_record* out, int max_records, int* n_out);
+int trace_begin(Trace& t, unsigned kind, int level, cudaStream_t s);  // slot or -1
+void trace_end(Trace& t, int slot, cudaStream_t s);
+
+}  // namespace pano

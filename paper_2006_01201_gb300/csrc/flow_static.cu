@@ -206,8 +206,8 @@ pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L
             pa.dst[si] = pyr[si][l];
             pa.dst_pitch[si] = lp[l];
         }
-        pa.h = hs[l - 1];
-        pa.w = ws[l - 1];
+        pa.h[0] = pa.h[1] = hs[l - 1];
+        pa.w[0] = pa.w[1] = ws[l - 1];
         pa.count = 2;
         if ((e = launch_pyr_down(pa, s)) != cudaSuccess)
             return sfail(PANO_ERR_CUDA, "pyramid launch: %s", cudaGetErrorString(e));

@@ -46,10 +46,10 @@ __device__ __forceinline__ float2 start_flow(const LkArgs& a, const LkDir& D, in
     return make_float2(2.f * fmaf(fy, bx - tx, tx), 2.f * fmaf(fy, by - ty, ty));
 }
 
+// One output tile (bx, by) of direction `dir` of one level.
 template <int RAD>
-__global__ void __launch_bounds__(kLkThreads) lk_level_kernel(LkArgs a) {
-    extern __shared__ float4 smem4[];
-    const LkDir D = a.dir[blockIdx.z];
+__device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, int by, float4* smem4) {
+    const LkDir& D = a.dir[dir];
     const int K = a.iters;
     const int halo = K * RAD;
     const int RW = a.tile_w + 2 * halo, RH = a.tile_h + 2 * halo;
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kLkThreads) lk_level_kernel(LkArgs a) {
     float2* sP = sU + N;                                  // per-sample products
     float2* sV = sP + N;                                  // column box sums
     float* sT = reinterpret_cast<float*>(sV + N);         // template
-    const int ox = blockIdx.x * a.tile_w - halo, oy = blockIdx.y * a.tile_h - halo;
+    const int ox = bx * a.tile_w - halo, oy = by * a.tile_h - halo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int w = a.w, h = a.h, pitchT = D.pitchT, pitchJ = D.pitchJ;
     const float* __restrict__ T = D.T;
@@ -90,8 +90,8 @@ __global__ void __launch_bounds__(kLkThreads) lk_level_kernel(LkArgs a) {
     __syncthreads();
 
     // Reference flow: the starting flow at the tile centre (inside the image).
-    const int cx = min(blockIdx.x * a.tile_w + a.tile_w / 2, w - 1);
-    const int cy = min(blockIdx.y * a.tile_h + a.tile_h / 2, h - 1);
+    const int cx = min(bx * a.tile_w + a.tile_w / 2, w - 1);
+    const int cy = min(by * a.tile_h + a.tile_h / 2, h - 1);
     const float2 ref = sU[(cy - oy) * RW + (cx - ox)];
 
     if (K > 0) {
@@ -184,10 +184,10 @@ __global__ void __launch_bounds__(kLkThreads) lk_level_kernel(LkArgs a) {
     const float2 add = (K > 0) ? ref : make_float2(0.f, 0.f);
     float2* __restrict__ uo = reinterpret_cast<float2*>(D.uout);
     for (int ty = warp; ty < a.tile_h; ty += nwarps) {
-        const int y = blockIdx.y * a.tile_h + ty;
+        const int y = by * a.tile_h + ty;
         if (y >= h) break;
         for (int tx = lane; tx < a.tile_w; tx += 32) {
-            const int x = blockIdx.x * a.tile_w + tx;
+            const int x = bx * a.tile_w + tx;
             if (x >= w) break;
             const float2 u = sU[(ty + halo) * RW + (tx + halo)];
             uo[(long long)y * D.uout_pitch + x] = make_float2(u.x + add.x, u.y + add.y);
@@ -196,10 +196,43 @@ __global__ void __launch_bounds__(kLkThreads) lk_level_kernel(LkArgs a) {
 }
 
 template <int RAD>
+__global__ void __launch_bounds__(kLkThreads) lk_level_kernel(const __grid_constant__ LkArgs a) {
+    extern __shared__ float4 smem4[];
+    lk_tile_item<RAD>(a, blockIdx.z, blockIdx.x, blockIdx.y, smem4);
+}
+
+// The same level of several strip pairs: blockIdx.z = 2 * pair + direction,
+// the x/y grid covers the largest pair and tiles beyond a smaller pair exit.
+template <int RAD>
+__global__ void __launch_bounds__(kLkThreads) lk_level_batch_kernel(const __grid_constant__ LkBatch b) {
+    extern __shared__ float4 smem4[];
+    const LkArgs& a = b.pair[blockIdx.z >> 1];
+    if ((int)blockIdx.x * a.tile_w >= a.w || (int)blockIdx.y * a.tile_h >= a.h) return;
+    lk_tile_item<RAD>(a, blockIdx.z & 1, blockIdx.x, blockIdx.y, smem4);
+}
+
+template <int RAD>
 cudaError_t launch_rad(const LkArgs& a, int ndirs, cudaStream_t s) {
     size_t smem = lk_smem_bytes(a.tile_w, a.tile_h, a.iters, a.radius);
     dim3 grid((a.w + a.tile_w - 1) / a.tile_w, (a.h + a.tile_h - 1) / a.tile_h, ndirs);
     lk_level_kernel<RAD><<<grid, kLkThreads, smem, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <int RAD>
+cudaError_t launch_rad_batch(const LkBatch& b, cudaStream_t s) {
+    const LkArgs& a0 = b.pair[0];
+    size_t smem = lk_smem_bytes(a0.tile_w, a0.tile_h, a0.iters, a0.radius);
+    int gx = 0, gy = 0;
+    for (int p = 0; p < b.n; ++p) {
+        const LkArgs& a = b.pair[p];
+        if (a.tile_w != a0.tile_w || a.tile_h != a0.tile_h || a.iters != a0.iters || a.radius != a0.radius)
+            return cudaErrorInvalidValue;
+        gx = max(gx, (a.w + a.tile_w - 1) / a.tile_w);
+        gy = max(gy, (a.h + a.tile_h - 1) / a.tile_h);
+    }
+    dim3 grid(gx, gy, 2 * b.n);
+    lk_level_batch_kernel<RAD><<<grid, kLkThreads, smem, s>>>(b);
     return cudaGetLastError();
 }
 
@@ -214,9 +247,13 @@ size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius) {
 cudaError_t lk_prepare(int max_smem_bytes) {
     cudaError_t e;
     if ((e = lk_stream_prepare(max_smem_bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(lk_level_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes)) != cudaSuccess) return e;
-    if ((e = cudaFuncSetAttribute(lk_level_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes)) != cudaSuccess) return e;
-    return cudaFuncSetAttribute(lk_level_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
+    const void* fns[] = {(const void*)lk_level_kernel<1>,       (const void*)lk_level_kernel<2>,
+                         (const void*)lk_level_kernel<3>,       (const void*)lk_level_batch_kernel<1>,
+                         (const void*)lk_level_batch_kernel<2>, (const void*)lk_level_batch_kernel<3>};
+    for (const void* f : fns)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes)) != cudaSuccess)
+            return e;
+    return cudaSuccess;
 }
 
 cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s) {
@@ -225,6 +262,16 @@ cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s) {
     if (lk_stream_supports(a.iters, a.radius) && (long long)a.w * a.h >= kStreamMinPixels)
         return launch_lk_stream(a, ndirs, s);
     return launch_lk_tile(a, ndirs, s);
+}
+
+cudaError_t launch_lk_tile_batch(const LkBatch& b, cudaStream_t s) {
+    if (b.n < 1 || b.n > kMaxBatch) return cudaErrorInvalidValue;
+    switch (b.pair[0].radius) {
+        case 1: return launch_rad_batch<1>(b, s);
+        case 2: return launch_rad_batch<2>(b, s);
+        case 3: return launch_rad_batch<3>(b, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_lk_tile(const LkArgs& a, int ndirs, cudaStream_t s) {

@@ -161,8 +161,11 @@ __device__ __forceinline__ void column_sums(const float2* __restrict__ sP, float
     for (int d = 0; d < 2 * RAD; ++d) hist[d * RW + rx] = p[CH + d];
 }
 
+// One work item: direction `dir`, band `bx` (BW output columns) and segment
+// `by` (rows [by * seg, by * seg + seg)) of the level described by `a`.
 template <int RAD, int K, int BW, int CH>
-__global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, int seg) {
+__device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx, int by, int seg,
+                                               unsigned char* smem) {
     using Geo = StreamGeom<RAD, K, BW, CH>;
     constexpr int RW = Geo::RW;
     constexpr int JW = Geo::JW;
@@ -171,7 +174,6 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
     constexpr int TX = kStreamThreads / CH;
     static_assert(TX * CH == kStreamThreads, "threads must tile the chunk rows");
     static_assert(RW <= kCsT0 && kCsT0 + 2 * RW <= kStreamThreads && CH % 2 == 0, "B_1 thread groups");
-    extern __shared__ __align__(16) unsigned char smem[];
     float* sT = reinterpret_cast<float*>(smem + Geo::kT);
     float2* sG = reinterpret_cast<float2*>(smem + Geo::kG);
     float2* sU = reinterpret_cast<float2*>(smem + Geo::kU);
@@ -187,14 +189,14 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
     float2* sFS = reinterpret_cast<float2*>(smem + Geo::kFS);    // staged coarse flow rows
     constexpr int TSW = Geo::TSW, TSH = Geo::TSH, FSW = Geo::FSW, FSH = Geo::FSH;
 
-    const LkDir D = a.dir[blockIdx.z];
+    const LkDir D = dir ? a.dir[1] : a.dir[0];
     const int w = a.w, h = a.h;
     const float lam = a.lambda;
     const float* __restrict__ T = D.T;
     const int pitchT = D.pitchT;
-    const int X0 = blockIdx.x * BW;
+    const int X0 = bx * BW;
     const int ox = X0 - K * RAD;
-    const int Y0 = blockIdx.y * seg;
+    const int Y0 = by * seg;
     const int Y1 = min(h, Y0 + seg);
     const int tid = threadIdx.x;
     const int ty = tid / TX, tx = tid - ty * TX;
@@ -466,20 +468,62 @@ __global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(LkArgs a, 
 }
 
 template <int RAD, int K, int BW, int CH>
+__global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_kernel(const __grid_constant__ LkArgs a, int seg) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    lk_stream_item<RAD, K, BW, CH>(a, blockIdx.z, blockIdx.x, blockIdx.y, seg, smem);
+}
+
+// Persistent form over several strip pairs at once: a fixed grid of CTAs
+// takes (pair, direction, band, segment) items from an atomic counter until
+// none are left. The counter only hands out indices; nothing waits on it.
+template <int RAD, int K, int BW, int CH>
+__global__ void __launch_bounds__(kStreamThreads, 1) lk_stream_batch_kernel(const __grid_constant__ LkBatch b) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = (int)atomicAdd(b.counter, 1u);
+        __syncthreads();
+        const int item = s_item;
+        __syncthreads();
+        if (item >= b.start[b.n]) break;
+        int p = 0;
+        while (p + 1 < b.n && item >= b.start[p + 1]) ++p;
+        const int local = item - b.start[p];
+        const int per_dir = b.nb[p] * b.nseg[p];
+        const int dir = local / per_dir, rem = local - dir * per_dir;
+        const int by = rem / b.nb[p], bx = rem - by * b.nb[p];
+        lk_stream_item<RAD, K, BW, CH>(b.pair[p], dir, bx, by, b.seg[p], smem);
+        __syncthreads();
+    }
+}
+
+// Segment height and count for one level: about 192+ rows per segment (the
+// first chunks of a segment are discarded work), in whole waves of one CTA
+// per SM; seg_rows > 0 overrides the target height.
+template <int CH>
+void stream_segments(int h, int per_row, int seg_rows, int* seg_out, int* nseg_out) {
+    const int sms = 152;
+    int seg;
+    if (seg_rows > 0) {
+        seg = seg_rows;
+    } else {
+        long long waves = (long long)per_row * h / (192LL * sms);
+        if (waves < 1) waves = 1;
+        int nseg = (int)(waves * sms / per_row);
+        if (nseg < 1) nseg = 1;
+        seg = (h + nseg - 1) / nseg;
+    }
+    if (seg < 2 * CH) seg = 2 * CH;
+    *seg_out = seg;
+    *nseg_out = (h + seg - 1) / seg;
+}
+
+template <int RAD, int K, int BW, int CH>
 cudaError_t launch_one(const LkArgs& a, int ndirs, cudaStream_t s) {
     using Geo = StreamGeom<RAD, K, BW, CH>;
     const int nb = (a.w + BW - 1) / BW;
-    const int per_row = nb * ndirs;
-    // segments of about 192+ rows (the first chunks of a segment are
-    // discarded work), in whole waves of one CTA per SM
-    const int sms = 152;
-    long long waves = (long long)per_row * a.h / (192LL * sms);
-    if (waves < 1) waves = 1;
-    int nseg = (int)(waves * sms / per_row);
-    if (nseg < 1) nseg = 1;
-    int seg = (a.h + nseg - 1) / nseg;
-    if (seg < 2 * CH) seg = 2 * CH;
-    nseg = (a.h + seg - 1) / seg;
+    int seg = 0, nseg = 0;
+    stream_segments<CH>(a.h, nb * ndirs, a.seg_rows, &seg, &nseg);
     dim3 grid(nb, nseg, ndirs);
     lk_stream_kernel<RAD, K, BW, CH><<<grid, kStreamThreads, Geo::bytes, s>>>(a, seg);
     return cudaGetLastError();
@@ -489,7 +533,10 @@ template <int RAD, int K, int BW, int CH>
 cudaError_t prepare_one(int max_smem) {
     using Geo = StreamGeom<RAD, K, BW, CH>;
     if (Geo::bytes > (size_t)max_smem) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(lk_stream_kernel<RAD, K, BW, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(lk_stream_kernel<RAD, K, BW, CH>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Geo::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(lk_stream_batch_kernel<RAD, K, BW, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)Geo::bytes);
 }
 
@@ -503,6 +550,36 @@ template <>
 struct RadCfg<2> { static constexpr int CH = 12; };
 template <>
 struct RadCfg<3> { static constexpr int CH = 8; };
+
+template <int RAD, int K, int BW, int CH>
+cudaError_t launch_batch_one(LkBatch b, int n_ctas, cudaStream_t s) {
+    using Geo = StreamGeom<RAD, K, BW, CH>;
+    b.start[0] = 0;
+    for (int p = 0; p < b.n; ++p) {
+        b.nb[p] = (b.pair[p].w + BW - 1) / BW;
+        stream_segments<CH>(b.pair[p].h, b.nb[p] * 2, b.pair[p].seg_rows, &b.seg[p], &b.nseg[p]);
+        b.start[p + 1] = b.start[p] + 2 * b.nb[p] * b.nseg[p];
+    }
+    int grid = n_ctas > 0 ? n_ctas : 152;
+    if (grid > b.start[b.n]) grid = b.start[b.n];
+    cudaError_t e = cudaMemsetAsync(b.counter, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    lk_stream_batch_kernel<RAD, K, BW, CH><<<grid, kStreamThreads, Geo::bytes, s>>>(b);
+    return cudaGetLastError();
+}
+
+template <int RAD>
+cudaError_t launch_rad_batch(const LkBatch& b, int n_ctas, cudaStream_t s) {
+    constexpr int CH = RadCfg<RAD>::CH;
+    switch (b.pair[0].iters) {
+        case 1: return launch_batch_one<RAD, 1, kBW, CH>(b, n_ctas, s);
+        case 2: return launch_batch_one<RAD, 2, kBW, CH>(b, n_ctas, s);
+        case 3: return launch_batch_one<RAD, 3, kBW, CH>(b, n_ctas, s);
+        case 4: return launch_batch_one<RAD, 4, kBW, CH>(b, n_ctas, s);
+        case 5: return launch_batch_one<RAD, 5, kBW, CH>(b, n_ctas, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
 
 template <int RAD>
 cudaError_t launch_rad_stream(const LkArgs& a, int ndirs, cudaStream_t s) {
@@ -537,6 +614,16 @@ cudaError_t lk_stream_prepare(int max_smem_bytes) {
     if ((e = prepare_rad_stream<1>(max_smem_bytes)) != cudaSuccess) return e;
     if ((e = prepare_rad_stream<2>(max_smem_bytes)) != cudaSuccess) return e;
     return prepare_rad_stream<3>(max_smem_bytes);
+}
+
+cudaError_t launch_lk_stream_batch(const LkBatch& b, int n_ctas, cudaStream_t s) {
+    if (b.n < 1 || b.n > kMaxBatch) return cudaErrorInvalidValue;
+    switch (b.pair[0].radius) {
+        case 1: return launch_rad_batch<1>(b, n_ctas, s);
+        case 2: return launch_rad_batch<2>(b, n_ctas, s);
+        case 3: return launch_rad_batch<3>(b, n_ctas, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_lk_stream(const LkArgs& a, int ndirs, cudaStream_t s) {

@@ -14,9 +14,9 @@ namespace {
 constexpr float kInv255 = 1.0f / 255.0f;
 
 // ---------------------------------------------------------------------------
-// Level 0: each thread converts 4 consecutive pixels of one row. Both strips
-// in one launch (blockIdx.z selects the strip; the descriptor is picked with
-// a select, not an indexed parameter load, so it stays in registers).
+// Level 0: each thread converts 4 consecutive pixels of one row. All strips
+// in one launch (blockIdx.z selects the strip; the grid-constant descriptor
+// is indexed in parameter space, without a local copy).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ float luma_at(const ImageDesc& in, const unsigned char* row, int x) {
     if (in.dtype == 0) {
@@ -31,11 +31,10 @@ __device__ __forceinline__ float luma_at(const ImageDesc& in, const unsigned cha
     return r[x];
 }
 
-__global__ void __launch_bounds__(256) luma_kernel(LumaArgs a) {
-    const bool second = blockIdx.z != 0;
-    const ImageDesc in = second ? a.in[1] : a.in[0];
-    float* out = second ? a.out[1] : a.out[0];
-    const int out_pitch = second ? a.out_pitch[1] : a.out_pitch[0];
+__global__ void __launch_bounds__(256) luma_kernel(const __grid_constant__ LumaArgs a) {
+    const ImageDesc& in = a.in[blockIdx.z];
+    float* out = a.out[blockIdx.z];
+    const int out_pitch = a.out_pitch[blockIdx.z];
     const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y;
     if (x >= in.w || y >= in.h) return;
@@ -74,22 +73,23 @@ constexpr int kPdTW = 32, kPdTH = 8;
 constexpr int kPdSW = 2 * kPdTW + 3;  // source columns 2*x0-2 .. 2*(x0+31)+2
 constexpr int kPdSH = 2 * kPdTH + 3;
 
-__global__ void __launch_bounds__(256) pyr_down_kernel(PyrDownArgs a) {
+__global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ PyrDownArgs a) {
     __shared__ float s_src[kPdSH][kPdSW + 1];
     __shared__ float s_v[kPdTH][kPdSW + 1];
-    const bool second = blockIdx.z != 0;
-    const float* __restrict__ src = second ? a.src[1] : a.src[0];
-    float* __restrict__ dst = second ? a.dst[1] : a.dst[0];
-    const int src_pitch = second ? a.src_pitch[1] : a.src_pitch[0];
-    const int dst_pitch = second ? a.dst_pitch[1] : a.dst_pitch[0];
-    const int hd = (a.h + 1) >> 1, wd = (a.w + 1) >> 1;
+    const int z = blockIdx.z;
+    const float* __restrict__ src = a.src[z];
+    float* __restrict__ dst = a.dst[z];
+    const int src_pitch = a.src_pitch[z], dst_pitch = a.dst_pitch[z];
+    const int h = a.h[z], w = a.w[z];
+    const int hd = (h + 1) >> 1, wd = (w + 1) >> 1;
     const int xd0 = blockIdx.x * kPdTW, yd0 = blockIdx.y * kPdTH;
+    if (xd0 >= wd || yd0 >= hd) return;  // a smaller plane of the batch
     const int sx0 = 2 * xd0 - 2, sy0 = 2 * yd0 - 2;
     const int tid = threadIdx.y * kPdTW + threadIdx.x;
     for (int i = tid; i < kPdSH * kPdSW; i += 256) {
         int r = i / kPdSW, c = i - r * kPdSW;
-        int sy = min(max(sy0 + r, 0), a.h - 1);
-        int sx = min(max(sx0 + c, 0), a.w - 1);
+        int sy = min(max(sy0 + r, 0), h - 1);
+        int sx = min(max(sx0 + c, 0), w - 1);
         s_src[r][c] = __ldg(src + (long long)sy * src_pitch + sx);
     }
     __syncthreads();
@@ -113,8 +113,12 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(PyrDownArgs a) {
 }  // namespace
 
 cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s) {
-    int h = max(a.in[0].h, a.count > 1 ? a.in[1].h : 0);
-    int w = max(a.in[0].w, a.count > 1 ? a.in[1].w : 0);
+    if (a.count < 1 || a.count > kMaxPlanes) return cudaErrorInvalidValue;
+    int h = 0, w = 0;
+    for (int i = 0; i < a.count; ++i) {
+        h = max(h, a.in[i].h);
+        w = max(w, a.in[i].w);
+    }
     dim3 block(64);
     dim3 grid((w + 4 * 64 - 1) / (4 * 64), h, a.count);
     luma_kernel<<<grid, block, 0, s>>>(a);
@@ -122,7 +126,12 @@ cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s) {
 }
 
 cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s) {
-    int hd = (a.h + 1) / 2, wd = (a.w + 1) / 2;
+    if (a.count < 1 || a.count > kMaxPlanes) return cudaErrorInvalidValue;
+    int hd = 0, wd = 0;
+    for (int i = 0; i < a.count; ++i) {
+        hd = max(hd, (a.h[i] + 1) / 2);
+        wd = max(wd, (a.w[i] + 1) / 2);
+    }
     dim3 block(kPdTW, kPdTH);
     dim3 grid((wd + kPdTW - 1) / kPdTW, (hd + kPdTH - 1) / kPdTH, a.count);
     pyr_down_kernel<<<grid, block, 0, s>>>(a);

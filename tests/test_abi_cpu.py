@@ -2,6 +2,7 @@
 function the header declares, and rejects bad arguments on the host before
 touching the device."""
 import ctypes
+import glob
 import os
 import re
 
@@ -10,7 +11,7 @@ import pytest
 from paper_2006_01201_gb300 import binding, build
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "pano_flow.h")
+HEADERS = sorted(glob.glob(os.path.join(ROOT, "include", "*.h")))
 
 
 @pytest.fixture(scope="module")
@@ -20,8 +21,11 @@ def lib():
 
 
 def declared_functions():
-    src = open(HEADER).read()
-    return re.findall(r"^PANO_API\s+[\w\s\*]+?\b(pano_\w+)\s*\(", src, flags=re.M)
+    names = []
+    for h in HEADERS:
+        src = open(h).read()
+        names += re.findall(r"^PANO_API\s+[\w\s\*]+?\b(pano_\w+)\s*\(", src, flags=re.M)
+    return names
 
 
 def test_header_declares_the_boundary():
@@ -103,3 +107,54 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(binding.PanoError):
         binding.load_library(str(tmp_path / "nope.so"))
+
+
+def _rig_desc(**kw):
+    d = binding.PanoRigDesc()
+    d.n_pairs, d.h, d.c, d.dtype = 2, 64, 3, binding.PANO_U8
+    d.canvas_h, d.canvas_w, d.canvas_y0 = 64, 200, 0
+    d.w[0], d.w[1] = 40, 50
+    d.canvas_x0[0], d.canvas_x0[1] = 0, 100
+    for k, v in kw.items():
+        if k in ("w", "canvas_x0"):
+            for i, x in enumerate(v):
+                getattr(d, k)[i] = x
+        else:
+            setattr(d, k, v)
+    return d
+
+
+_INV, _UNS = binding.PANO_ERR_INVALID_ARG, binding.PANO_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("bad,status", [(dict(n_pairs=0), _INV), (dict(n_pairs=9), _INV), (dict(h=0), _INV),
+                                        (dict(c=2), _UNS), (dict(dtype=7), _INV),
+                                        (dict(dtype=binding.PANO_BF16), _UNS), (dict(canvas_w=0), _INV),
+                                        (dict(canvas_y0=1), _INV), (dict(canvas_y0=-1), _INV),
+                                        (dict(w=[0, 50]), _INV), (dict(w=[40, 201]), _INV),
+                                        (dict(canvas_x0=[200, 0]), _INV), (dict(canvas_x0=[-1, 0]), _INV)])
+def test_rig_create_rejects_bad_geometry_before_any_device_call(lib, bad, status):
+    p = binding.PanoParams()
+    lib.pano_flow_params_default(ctypes.byref(p))
+    out = ctypes.c_void_p(5)
+    d = _rig_desc(**bad)
+    assert lib.pano_rig_create(ctypes.byref(p), ctypes.byref(d), ctypes.byref(out)) == status
+    assert out.value is None
+    assert lib.pano_last_error(None)
+
+
+def test_rig_null_arguments(lib):
+    p = binding.PanoParams()
+    lib.pano_flow_params_default(ctypes.byref(p))
+    d = _rig_desc()
+    out = ctypes.c_void_p()
+    assert lib.pano_rig_create(None, ctypes.byref(d), ctypes.byref(out)) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_rig_create(ctypes.byref(p), None, ctypes.byref(out)) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_rig_create(ctypes.byref(p), ctypes.byref(d), None) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_rig_run(None, None, None, None, None, None, 0, None) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_rig_autotune(None, None, None, 1, None) == binding.PANO_ERR_INVALID_ARG
+    t = binding.PanoRigTuning()
+    assert lib.pano_rig_get_tuning(None, 0, ctypes.byref(t)) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_rig_set_tuning(None, 0, ctypes.byref(t)) == binding.PANO_ERR_INVALID_ARG
+    assert lib.pano_rig_destroy(None) == binding.PANO_OK
+    assert lib.pano_rig_launches(None) == 0 and lib.pano_rig_graph_captures(None) == 0

@@ -69,3 +69,15 @@ def test_reference_arm_on_nonzero_rank_exits_quietly(monkeypatch, capsys):
 def test_warmup_below_three_is_rejected():
     with pytest.raises(SystemExit):
         bench.main(["--warmup", "2"])
+
+
+def test_rig_level_kernels_follow_the_size_rule_and_forced_kinds():
+    widths = bench.RIG_WORKLOAD["widths"]
+    plan = bench.rig_level_kernels(4000, widths, 6, [bench.PANO_LK_AUTO] * 6)
+    # level 3 is 500 rows: widths >= 200 give >= 100000 pixels
+    assert plan[3] == [("lk_stream_batch_kernel", [5, 6, 7]), ("lk_level_batch_kernel", [0, 1, 2, 3, 4])]
+    assert plan[0] == [("lk_stream_batch_kernel", list(range(8)))]
+    assert plan[5] == [("lk_level_batch_kernel", list(range(8)))]
+    forced = bench.rig_level_kernels(4000, widths, 6, [bench.PANO_LK_TILE] + [bench.PANO_LK_STREAM] * 5)
+    assert forced[0] == [("lk_level_batch_kernel", list(range(8)))]
+    assert all(p == [("lk_stream_batch_kernel", list(range(8)))] for p in forced[1:])
