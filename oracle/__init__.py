@@ -62,6 +62,9 @@ def lib():
             "oracle_lk_step": ([_D, _D, i, i, _D, i, d], None),
             "oracle_upsample_flow": ([_D, i, i, _D, i, i], None),
             "oracle_pyramid": ([_D, i, i, i, _D], None),
+            "oracle_pyramid_stored": ([_D, i, i, i, i, _D], None),
+            "oracle_round_storage": ([_D, l, i], None),
+            "oracle_flow_pair_stored": ([_D, _D, i, i, i, i, i, d, i, _D, _D], None),
             "oracle_flow_dir": ([_D, _D, i, i, i, i, i, d, _D], None),
             "oracle_flow_pair": ([_D, _D, i, i, i, i, i, d, _D, _D], None),
             "oracle_blend_coeff": ([_U8, i, i, _D], None),
@@ -103,6 +106,18 @@ class Params:
     lam: float = 1e-2
     soft_sharpness: float = 10.0
     flow_mag_coef: float = 20.0
+    pyr_fmt: int = 0      # storage of the pyramid levels: FMT_EXACT, FMT_BF16 or FMT_F16
+
+
+# storage formats of the pyramid levels (oracle_round_storage)
+FMT_EXACT, FMT_BF16, FMT_F16 = 0, 1, 2
+
+
+def round_storage(a, fmt: int) -> np.ndarray:
+    """Every value rounded to the nearest value of the format (ties to even)."""
+    out = _f64(a).copy()
+    lib().oracle_round_storage(_d(out), out.size, int(fmt))
+    return out
 
 
 def set_num_threads(n: int) -> None:
@@ -148,12 +163,15 @@ def level_shapes(h: int, w: int, levels: int):
     return shapes
 
 
-def pyramid(Y: np.ndarray, levels: int) -> list:
+def pyramid(Y: np.ndarray, levels: int, fmt: int = FMT_EXACT) -> list:
     a = _f64(Y)
     h, w = a.shape
     shapes = level_shapes(h, w, levels)
     flat = np.empty(sum(s[0] * s[1] for s in shapes), dtype=np.float64)
-    lib().oracle_pyramid(_d(a), h, w, levels, _d(flat))
+    if fmt == FMT_EXACT:
+        lib().oracle_pyramid(_d(a), h, w, levels, _d(flat))
+    else:
+        lib().oracle_pyramid_stored(_d(a), h, w, levels, int(fmt), _d(flat))
     out, off = [], 0
     for sh, sw in shapes:
         out.append(flat[off:off + sh * sw].reshape(sh, sw).copy())
@@ -221,7 +239,11 @@ def flow_pair_luma(YL: np.ndarray, YR: np.ndarray, p: Params):
     h, w = yl.shape
     lr = np.empty((h, w, 2), dtype=np.float64)
     rl = np.empty((h, w, 2), dtype=np.float64)
-    lib().oracle_flow_pair(_d(yl), _d(yr), h, w, p.levels, p.iters, p.radius, p.lam, _d(lr), _d(rl))
+    if p.pyr_fmt == FMT_EXACT:
+        lib().oracle_flow_pair(_d(yl), _d(yr), h, w, p.levels, p.iters, p.radius, p.lam, _d(lr), _d(rl))
+    else:
+        lib().oracle_flow_pair_stored(_d(yl), _d(yr), h, w, p.levels, p.iters, p.radius, p.lam, int(p.pyr_fmt),
+                                      _d(lr), _d(rl))
     return lr, rl
 
 

@@ -286,19 +286,61 @@ static void level_sizes(int h, int w, int levels, int* hs, int* ws)
     for (int l = 1; l < levels; ++l) { hs[l] = (hs[l - 1] + 1) / 2; ws[l] = (ws[l - 1] + 1) / 2; }
 }
 
+/* ---------------------------------------------------------------------------
+ * Storage precision of the pyramid levels. Not a step of the paper (it states
+ * no precision): a build extension that keeps the levels in a 16-bit format.
+ * fmt 0 = exact (no rounding), 1 = bfloat16, 2 = IEEE 754 binary16.
+ * A format with p significand bits (the leading one included) and smallest
+ * normal exponent emin holds, for |v| in [2^e, 2^(e+1)) with e >= emin, the
+ * multiples of 2^(e - p + 1); below 2^emin (subnormals) the multiples of
+ * 2^(emin - p + 1). Rounding is to the nearest such value, ties to the even
+ * multiple; results beyond the largest finite value become +-infinity.
+ *   bfloat16: p = 8, emin = -126, largest (2 - 2^-7) 2^127
+ *   binary16: p = 11, emin = -14, largest (2 - 2^-10) 2^15 = 65504
+ * ------------------------------------------------------------------------- */
+static double round_to_format(double v, int p, int emin, double maxv)
+{
+    if (v == 0.0 || !isfinite(v)) return v;
+    int e;
+    frexp(fabs(v), &e);              /* |v| = m 2^e with m in [0.5, 1): leading bit 2^(e-1) */
+    int lead = e - 1;
+    if (lead < emin) lead = emin;    /* subnormal range: fixed spacing */
+    double ulp = ldexp(1.0, lead - (p - 1));
+    double r = nearbyint(v / ulp) * ulp;   /* default rounding mode: to nearest, ties to even */
+    if (fabs(r) > maxv) return v > 0 ? INFINITY : -INFINITY;
+    return r;
+}
+
+void oracle_round_storage(double* a, long n, int fmt)
+{
+    if (fmt == 0) return;
+    int p = fmt == 1 ? 8 : 11;
+    int emin = fmt == 1 ? -126 : -14;
+    double maxv = fmt == 1 ? ldexp(2.0 - ldexp(1.0, -7), 127) : 65504.0;
+    for (long i = 0; i < n; ++i) a[i] = round_to_format(a[i], p, emin, maxv);
+}
+
 /* Pyramid of a single-channel image: levels planes, level 0 = Y. out holds
-   the planes back to back (level 0 first). */
-void oracle_pyramid(const double* Y, int h, int w, int levels, double* out)
+   the planes back to back (level 0 first). With a storage format every level
+   is rounded as it is stored, and the next REDUCE reads the stored level. */
+void oracle_pyramid_stored(const double* Y, int h, int w, int levels, int fmt, double* out)
 {
     int hs[32], ws[32];
     level_sizes(h, w, levels, hs, ws);
     memcpy(out, Y, (size_t)h * w * sizeof(double));
+    oracle_round_storage(out, (long)h * w, fmt);
     double* prev = out;
     for (int l = 1; l < levels; ++l) {
         double* cur = prev + (size_t)hs[l - 1] * ws[l - 1];
         oracle_pyr_down(prev, hs[l - 1], ws[l - 1], cur);
+        oracle_round_storage(cur, (long)hs[l] * ws[l], fmt);
         prev = cur;
     }
+}
+
+void oracle_pyramid(const double* Y, int h, int w, int levels, double* out)
+{
+    oracle_pyramid_stored(Y, h, w, levels, 0, out);
 }
 
 /* ---------------------------------------------------------------------------
@@ -336,8 +378,8 @@ void oracle_flow_dir(const double* Tpyr, const double* Jpyr, int h, int w, int l
  * same procedure, so the pair differs only through the data ("asymmetric").
  * YL, YR: (h, w) luma. flowLR, flowRL: (h, w, 2).
  * ------------------------------------------------------------------------- */
-void oracle_flow_pair(const double* YL, const double* YR, int h, int w, int levels, int iters,
-                      int r, double lambda, double* flowLR, double* flowRL)
+void oracle_flow_pair_stored(const double* YL, const double* YR, int h, int w, int levels, int iters,
+                             int r, double lambda, int fmt, double* flowLR, double* flowRL)
 {
     int hs[32], ws[32];
     level_sizes(h, w, levels, hs, ws);
@@ -345,11 +387,17 @@ void oracle_flow_pair(const double* YL, const double* YR, int h, int w, int leve
     for (int l = 0; l < levels; ++l) tot += (size_t)hs[l] * ws[l];
     double* PL = (double*)malloc(tot * sizeof(double));
     double* PR = (double*)malloc(tot * sizeof(double));
-    oracle_pyramid(YL, h, w, levels, PL);
-    oracle_pyramid(YR, h, w, levels, PR);
+    oracle_pyramid_stored(YL, h, w, levels, fmt, PL);
+    oracle_pyramid_stored(YR, h, w, levels, fmt, PR);
     oracle_flow_dir(PL, PR, h, w, levels, iters, r, lambda, flowLR);
     oracle_flow_dir(PR, PL, h, w, levels, iters, r, lambda, flowRL);
     free(PL); free(PR);
+}
+
+void oracle_flow_pair(const double* YL, const double* YR, int h, int w, int levels, int iters,
+                      int r, double lambda, double* flowLR, double* flowRL)
+{
+    oracle_flow_pair_stored(YL, YR, h, w, levels, iters, r, lambda, 0, flowLR, flowRL);
 }
 
 /* ---------------------------------------------------------------------------

@@ -14,6 +14,7 @@ import pytest
 import oracle
 from tests import test_oracle_pins as pins
 from tests import test_oracle_refine_pins as rpins
+from tests import test_oracle_storage_pins as spins
 
 SRC = os.path.join(os.path.dirname(oracle.__file__), "pano_oracle.c")
 
@@ -49,6 +50,10 @@ MUTANTS = [
     ("energy grad J tap weight", "PIX(gJ, w, ya, xb) += g * (1.0 - fy) * fx;", "PIX(gJ, w, ya, xb) += g * fy * fx;"),
     ("energy grad derivative axis", "*dx = (1.0 - fy) * (i10 - i00) + fy * (i11 - i01);",
      "*dx = (1.0 - fx) * (i10 - i00) + fx * (i11 - i01);"),
+    ("bfloat16 significand bits", "int p = fmt == 1 ? 8 : 11;", "int p = fmt == 1 ? 9 : 11;"),
+    ("storage rounds down", "double r = nearbyint(v / ulp) * ulp;", "double r = floor(v / ulp) * ulp;"),
+    ("storage without subnormal spacing", "if (lead < emin) lead = emin;", "if (0) lead = emin;"),
+    ("stored level not rounded", "        oracle_round_storage(cur, (long)hs[l] * ws[l], fmt);\n", "\n"),
     ("reduce adjoint weight", "PIX(gsrc, w, sy, sx) += k[ty + 2] * k[tx + 2] * g;",
      "PIX(gsrc, w, sy, sx) += k[ty + 2] * k[ty + 2] * g;"),
 ]
@@ -76,6 +81,11 @@ PIN_TESTS = [
     lambda: rpins.test_smoothness_energy_closed_form(),
     lambda: rpins.test_energy_and_gradients_vanish_on_identical_images_and_zero_flow(),
     lambda: [rpins.test_reduce_transpose_dot_product_identity(s) for s in [(7, 9), (13, 2)]],
+    lambda: spins.test_binary16_rounding_matches_numpy(),
+    lambda: spins.test_bfloat16_rounding_matches_torch_on_float32_inputs(),
+    lambda: spins.test_ties_go_to_the_even_neighbour(),
+    lambda: [spins.test_stored_pyramid_is_representable_and_close_to_the_exact_one(f, p)
+             for f, p in [(oracle.FMT_BF16, 8), (oracle.FMT_F16, 11)]],
 ]
 
 
