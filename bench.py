@@ -55,27 +55,28 @@ def level_pixels(h: int, w: int, levels: int):
     return out
 
 
-def lk_alg_bytes(h: int, w: int, levels: int):
+def lk_alg_bytes(h: int, w: int, levels: int, elem: int = 4):
     """Algorithmic bytes of each LK level launch (both directions).
 
     Per direction and level pixel: read the template and target levels
-    (4 + 4 B), read the coarse flow (8 B per coarse pixel = 2 B per fine
+    (2 elem B), read the coarse flow (8 B per coarse pixel = 2 B per fine
     pixel; none at the coarsest level), write the flow (8 B).
     """
     npx = level_pixels(h, w, levels)
     out = []
     for l, n in enumerate(npx):
         coarse = 8 * npx[l + 1] if l + 1 < levels else 0
-        out.append(2 * (8 * n + coarse + 8 * n))
+        out.append(2 * (2 * elem * n + coarse + 8 * n))
     return out
 
 
-def path_alg_bytes(h: int, w: int, c: int, levels: int, in_bytes: int = 1):
-    """Algorithmic bytes of one step of the whole path (each array once)."""
+def path_alg_bytes(h: int, w: int, c: int, levels: int, in_bytes: int = 1, elem: int = 4):
+    """Algorithmic bytes of one step of the whole path (each array once);
+    elem = bytes of one stored pyramid element."""
     npx = level_pixels(h, w, levels)
     n = h * w
-    pyramid = 2 * c * in_bytes * n + 2 * 4 * sum(npx) + 2 * 4 * sum(npx[:-1])  # read strips, write levels, re-read for REDUCE
-    flow = sum(lk_alg_bytes(h, w, levels))
+    pyramid = 2 * c * in_bytes * n + 2 * elem * sum(npx) + 2 * elem * sum(npx[:-1])  # read strips, write levels, re-read for REDUCE
+    flow = sum(lk_alg_bytes(h, w, levels, elem))
     blend = 2 * c * in_bytes * n + 16 * n + c * in_bytes * n
     return pyramid + flow + blend
 
@@ -85,6 +86,8 @@ RIG_WORKLOAD = {"workload": "rig_8x4000x{800..2000}_rgb_u8_lv6_canvas_9000x4000"
                 "iters": 5, "radius": 2, "dmax": 24.0, "canvas": [4000, 9000],
                 "canvas_x0": [1125 * k for k in range(8)]}
 PANO_LK_AUTO, PANO_LK_STREAM, PANO_LK_TILE = 0, 1, 2
+# --pyr-dtype: (pano_dtype of the pyramid storage, oracle storage format, bytes per stored element)
+PYR_DTYPES = {"f32": (1, 0, 4), "bf16": (2, 1, 2), "f16": (3, 2, 2)}
 
 
 def rig_level_kernels(h: int, widths, levels: int, kernels):
@@ -276,7 +279,9 @@ def run_gpu(args):
     pkg.load_library()
     h, w, c, levels = WORKLOAD["h"], WORKLOAD["w"], WORKLOAD["channels"], WORKLOAD["levels"]
     pair = synth.pair_fullres_rgb(seed=1 + rank, h=h, w=w, levels=levels)
-    ctx = pkg.FlowContext(pkg.Params(levels=levels, iters=WORKLOAD["iters"], radius=WORKLOAD["radius"]),
+    pyr_code, pyr_fmt, elem = PYR_DTYPES[args.pyr_dtype]
+    ctx = pkg.FlowContext(pkg.Params(levels=levels, iters=WORKLOAD["iters"], radius=WORKLOAD["radius"],
+                                     pyr_dtype=pyr_code),
                           max_h=h, max_w=w, max_c=c)
     L = torch.from_numpy(pair.L).to(dev)
     R = torch.from_numpy(pair.R).to(dev)
@@ -325,7 +330,7 @@ def run_gpu(args):
     ctx.trace_enable(0, 0)
     names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "blend_kernel"}
     npx = level_pixels(h, w, levels)
-    lk_bytes = lk_alg_bytes(h, w, levels)
+    lk_bytes = lk_alg_bytes(h, w, levels, elem)
     per_kind = {}
     stream_bytes = 0.0
     for kind, lev, ms in recs:
@@ -358,7 +363,7 @@ def run_gpu(args):
                 "traffic": TRAFFIC_PER_LAUNCH.get(dominant), "kernel": dominant,
                 "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                 "launches_per_step": launches_per_step, "peak_source": f"{peak_src} hbm_gbs"}
-    path_bytes = path_alg_bytes(h, w, c, levels)
+    path_bytes = path_alg_bytes(h, w, c, levels, elem=elem)
     path_gbs = path_bytes / (total_ms / args.steps * 1e-3) / 1e9
 
     # --- end to end: pinned host strips in, F back to pinned host memory
@@ -391,7 +396,7 @@ def run_gpu(args):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(WORKLOAD, l2="flushed between steps (256 MB write, untimed)",
-                               parallelism=f"replicas{world}"),
+                               parallelism=f"replicas{world}", pyr_dtype=args.pyr_dtype),
                 "roofline": roofline,
                 "path": {"alg_bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / peak},
                 "kernels": per_kind, "dominant_kernel": dominant,
@@ -408,6 +413,9 @@ def run_gpu(args):
             e_lr = float(np.hypot(*(g_lr - olr).transpose(2, 0, 1)).mean())
             e_rl = float(np.hypot(*(g_rl - orl).transpose(2, 0, 1)).mean())
             line["epe_vs_oracle"] = {"LtoR_mean_px": e_lr, "RtoL_mean_px": e_rl}
+            if pyr_fmt:
+                line["half_precision"] = half_precision_report(pkg, pair, levels, pyr_fmt, g_lr, g_rl,
+                                                               F.cpu().numpy(), olr, orl, dev)
             v, cores, desc, secs = time_oracle(pair, levels, budget_s=args.cpu_budget)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
                                     "seconds": secs, "full_pair_flow_s": t_full}
@@ -418,6 +426,37 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+def half_precision_report(pkg, pair, levels, pyr_fmt, g_lr, g_rl, g_F, olr, orl, dev):
+    """Errors of 16-bit pyramid storage: flows against the exact FP64 oracle,
+    the storage-matched oracle and the float32 GPU path; blended pixels
+    against the float32 GPU path and the oracle."""
+    import numpy as np
+    import torch
+    import oracle
+
+    def mean_epe(a, b):
+        return float(np.hypot(*(a - b).transpose(2, 0, 1)).mean())
+
+    h, w = pair.L.shape[:2]
+    c = pair.L.shape[2] if pair.L.ndim == 3 else 1
+    with pkg.FlowContext(pkg.Params(levels=levels), max_h=h, max_w=w, max_c=c) as ctx32:
+        lr32, rl32, F32 = ctx32.stitch_pair(torch.from_numpy(pair.L).to(dev), torch.from_numpy(pair.R).to(dev))
+        torch.cuda.synchronize()
+        lr32, rl32, F32 = lr32.cpu().numpy(), rl32.cpu().numpy(), F32.cpu().numpy()
+    slr, srl = oracle.flow_pair(pair.L, pair.R, oracle.Params(levels=levels, pyr_fmt=pyr_fmt))
+    Fo = oracle.quantize_u8(oracle.blend(pair.L, pair.R, olr, orl, oracle.Params(levels=levels)))
+    d32 = np.abs(g_F.astype(int) - F32.astype(int))
+    do = np.abs(g_F.astype(int) - Fo.astype(int))
+    return {"epe_vs_exact_oracle": [mean_epe(g_lr, olr), mean_epe(g_rl, orl)],
+            "epe_vs_storage_oracle": [mean_epe(g_lr, slr), mean_epe(g_rl, srl)],
+            "epe_vs_gpu_f32": [mean_epe(g_lr, lr32), mean_epe(g_rl, rl32)],
+            "gpu_f32_epe_vs_exact_oracle": [mean_epe(lr32, olr), mean_epe(rl32, orl)],
+            "F_u8_vs_gpu_f32": {"max_lsb": int(d32.max()), "mean_lsb": float(d32.mean()),
+                                "frac_gt_1lsb": float((d32 > 1).mean())},
+            "F_u8_vs_exact_oracle": {"max_lsb": int(do.max()), "mean_lsb": float(do.mean()),
+                                     "frac_gt_1lsb": float((do > 1).mean())}}
 
 
 def run_refine(args):
@@ -501,7 +540,8 @@ def run_rig(args):
     W = RIG_WORKLOAD
     h, widths, c, levels = W["h"], W["widths"], W["channels"], W["levels"]
     pairs = synth.rig_pairs(h=h, widths=widths, dmax=W["dmax"], levels=levels, seed0=100 + 8 * rank)
-    params = pkg.Params(levels=levels, iters=W["iters"], radius=W["radius"])
+    pyr_code, pyr_fmt, elem = PYR_DTYPES[args.pyr_dtype]
+    params = pkg.Params(levels=levels, iters=W["iters"], radius=W["radius"], pyr_dtype=pyr_code)
     rig = binding.Rig(params, h, widths, c=c, dtype=torch.uint8, canvas_hw=tuple(W["canvas"]),
                       canvas_x0=W["canvas_x0"])
     Ls = [torch.from_numpy(p.L).to(dev) for p in pairs]
@@ -555,7 +595,7 @@ def run_rig(args):
     names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "rig_blend_kernel"}
     per_kind, lk_seen = {}, {}
     stream_bytes = 0.0
-    lk_bytes = [lk_alg_bytes(h, w, levels) for w in widths]
+    lk_bytes = [lk_alg_bytes(h, w, levels, elem) for w in widths]
     for kind, lev, ms in recs:
         if kind == 4:
             i = lk_seen.get(lev, 0) % len(plan[lev])
@@ -583,7 +623,35 @@ def run_rig(args):
                 "traffic": TRAFFIC_PER_LAUNCH.get(dominant), "kernel": dominant,
                 "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                 "launches_per_step": dk["launches"] / args.steps, "peak_source": f"{peak_src} hbm_gbs"}
-    path_bytes = sum(path_alg_bytes(h, w, c, levels) for w in widths)
+    path_bytes = sum(path_alg_bytes(h, w, c, levels, elem=elem) for w in widths)
+
+    def time_rig(other):
+        """CUDA-event time of K graph replays of another rig on the same strips."""
+        cv = other.new_canvas(dev)
+        for _ in range(args.warmup):
+            flush.zero_()
+            other.run(Ls, Rs, canvas=cv, use_graph=True, stream=stream)
+        torch.cuda.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            other.run(Ls, Rs, canvas=cv, use_graph=True, stream=stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        return reduce_max(sum(a.elapsed_time(b) for a, b in evs), world), cv
+
+    fp32_form = None
+    if pyr_fmt:
+        # the float32 batched form beside the 16-bit one, tuned the same way
+        rig32 = binding.Rig(pkg.Params(levels=levels, iters=W["iters"], radius=W["radius"]), h, widths, c=c,
+                            dtype=torch.uint8, canvas_hw=tuple(W["canvas"]), canvas_x0=W["canvas_x0"])
+        if not args.no_autotune:
+            rig32.autotune(Ls, Rs, reps=3, stream=stream)
+        ms32, canvas32 = time_rig(rig32)
+        fp32_form = {"value": throughput(npx, args.steps, world, ms32), "unit": UNIT,
+                     "ms_per_step": ms32 / args.steps}
 
     # --- the single-pair form on the same strips: 8 x (flow_pair + blend_pair)
     ctx = pkg.FlowContext(params, max_h=h, max_w=max(widths), max_c=c)
@@ -640,13 +708,14 @@ def run_rig(args):
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(W, l2="flushed between steps (256 MB write, untimed); inputs 262 MB > L2",
-                               parallelism=f"replicas{world}", graph=True),
+                               parallelism=f"replicas{world}", graph=True, pyr_dtype=args.pyr_dtype),
                 "roofline": roofline,
                 "path": {"alg_bytes_per_step": path_bytes,
                          "achieved_gbs": path_bytes / (total_ms / args.steps * 1e-3) / 1e9},
                 "kernels": per_kind, "dominant_kernel": dominant,
                 "single_pair_form": {"value": throughput(npx, args.steps, world, pair_ms), "unit": UNIT,
                                      "ms_per_step": pair_ms / args.steps},
+                "fp32_batched_form": fp32_form,
                 "autotune": {"seconds": tune_s, "levels": tunings},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
@@ -659,6 +728,19 @@ def run_rig(args):
                 "pair": 0,
                 "LtoR_mean_px": float(np.hypot(*(g_lr - olr).transpose(2, 0, 1)).mean()),
                 "RtoL_mean_px": float(np.hypot(*(g_rl - orl).transpose(2, 0, 1)).mean())}
+            if pyr_fmt:
+                # pair 1 owns its whole canvas span (columns 1125 .. 2074): pair 0's
+                # first columns are overwritten by pair 7, which wraps around the seam
+                x1 = W["canvas_x0"][1]
+                F1 = canvas[:, x1:x1 + widths[1]].cpu().numpy()
+                h_lr, h_rl = (t.cpu().numpy() for t in rig.flows(1))
+                x_lr, x_rl = oracle.flow_pair(pairs[1].L, pairs[1].R, oracle.Params(levels=levels))
+                line["half_precision"] = half_precision_report(pkg, pairs[1], levels, pyr_fmt, h_lr, h_rl, F1,
+                                                               x_lr, x_rl, dev)
+                line["half_precision"]["pair"] = 1
+                line["half_precision"]["canvas_u8_vs_fp32_rig"] = {
+                    "max_lsb": int((canvas.int() - canvas32.int()).abs().max()),
+                    "mean_lsb": float((canvas.int() - canvas32.int()).abs().float().mean())}
             v, cores, desc, secs = time_oracle(pairs[0], levels, budget_s=args.cpu_budget)
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": desc.replace("of the pair", "of rig pair 0 (4000x800)"),
@@ -684,6 +766,8 @@ def main(argv=None):
                     help="pair: the 4000x1500 overlap pair (default); rig: the 8-pair 360-degree rig; "
                          "refine_1024: the differentiable refinement")
     ap.add_argument("--no-autotune", action="store_true", help="rig: keep the default tuning")
+    ap.add_argument("--pyr-dtype", default="f32", choices=sorted(PYR_DTYPES),
+                    help="storage of the pyramid levels (arithmetic stays FP32)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

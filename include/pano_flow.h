@@ -70,8 +70,8 @@ typedef enum pano_status {
 typedef enum pano_dtype {
     PANO_U8 = 0,
     PANO_F32 = 1,
-    PANO_BF16 = 2,   /* reserved */
-    PANO_F16 = 3     /* reserved */
+    PANO_BF16 = 2,   /* pyramid storage only (pano_flow_params.pyr_dtype) */
+    PANO_F16 = 3     /* pyramid storage only (pano_flow_params.pyr_dtype) */
 } pano_dtype;
 
 typedef struct pano_image {
@@ -91,7 +91,9 @@ typedef struct pano_flow_params {
     float lambda;         /* damping towards the current flow, >= 0 (default 1e-2) */
     float soft_sharpness; /* kSoftmaxSharpness of Code 1 (default 10) */
     float flow_mag_coef;  /* kFlowMagCoef of Code 1 (default 20) */
-    int pyr_dtype;        /* storage of pyramid levels; PANO_F32 only */
+    int pyr_dtype;        /* storage of the pyramid levels, luma included: PANO_F32 (default),
+                             PANO_BF16 or PANO_F16 (rounded to nearest even when stored; all
+                             arithmetic stays FP32). Not a choice the paper makes */
 } pano_flow_params;
 
 typedef struct pano_flow_ctx pano_flow_ctx;
@@ -101,11 +103,12 @@ PANO_API void pano_flow_params_default(pano_flow_params* p);
 
 /* Create a context for strips of at most max_h x max_w pixels and max_c
  * channels on the current device, and allocate its scratch:
- * two pyramids of float32 levels (~ 2 * 4 * (4/3) * max_h * max_w bytes) and
+ * two pyramids of pyr_dtype levels (~ 2 * e * (4/3) * max_h * max_w bytes, e = 4
+ * for PANO_F32 and 2 for the 16-bit types) and
  * the coarse-level flows of both directions (~ 2 * 8 * (1/3) * max_h * max_w
  * bytes). *out receives the context; on failure *out is NULL.
  * Errors: INVALID_ARG (null p/out, parameters out of range, sizes < 1),
- * UNSUPPORTED (pyr_dtype other than PANO_F32), OOM, CUDA. */
+ * UNSUPPORTED (sizes beyond 32-bit offsets), OOM, CUDA. */
 PANO_API pano_status pano_flow_create(const pano_flow_params* p, int max_h, int max_w, int max_c,
                              pano_flow_ctx** out);
 
@@ -201,7 +204,8 @@ PANO_API pano_status pano_stage_pyr_down_adjoint(const float* gdst, int h, int w
  *               Calls whose work overlaps on the GPU race on the array:
  *               order them on one stream (or with events).
  * Arguments, flows and errors are those of pano_flow_pair; `params` replaces
- * the context.
+ * the context and must keep float32 pyramids (pyr_dtype PANO_F32; UNSUPPORTED
+ * otherwise).
  * ---------------------------------------------------------------------- */
 #define PANO_STATIC_SCRATCH_BYTES (16u * 1024u * 1024u)
 

@@ -82,7 +82,8 @@ typedef struct pano_rig pano_rig;
  * every pair (used when a call passes no flow buffers) and a private
  * capture stream. Every level starts with PANO_LK_AUTO tuning.
  * Errors: INVALID_ARG (null argument, parameters or geometry out of range),
- * UNSUPPORTED (pyr_dtype, sizes beyond 32-bit offsets), OOM, CUDA. */
+ * UNSUPPORTED (sizes beyond 32-bit offsets), OOM, CUDA. Pyramids are stored as
+ * p->pyr_dtype (see pano_flow_params). */
 PANO_API pano_status pano_rig_create(const pano_flow_params* p, const pano_rig_desc* d, pano_rig** out);
 
 /* Flows of every pair and, if canvas != NULL, their blends placed on the

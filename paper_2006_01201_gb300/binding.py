@@ -145,10 +145,11 @@ class Params:
     lam: float = 1e-2
     soft_sharpness: float = 10.0
     flow_mag_coef: float = 20.0
+    pyr_dtype: int = PANO_F32     # storage of the pyramid levels: PANO_F32, PANO_BF16 or PANO_F16
 
     def to_c(self) -> PanoParams:
         return PanoParams(self.levels, self.iters, self.radius, self.lam, self.soft_sharpness,
-                          self.flow_mag_coef, PANO_F32)
+                          self.flow_mag_coef, self.pyr_dtype)
 
 
 def _torch():

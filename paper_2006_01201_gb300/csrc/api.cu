@@ -41,6 +41,10 @@ size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 int elem_size(int dtype) { return dtype == PANO_U8 ? 1 : (dtype == PANO_F32 ? 4 : 2); }
 
+int pyr_type(int pyr_dtype) {
+    return pyr_dtype == PANO_BF16 ? kPyrBF16 : (pyr_dtype == PANO_F16 ? kPyrF16 : kPyrF32);
+}
+
 pano_status check_image(const pano_image* im, const char* name) {
     if (!im) return fail(PANO_ERR_INVALID_ARG, "%s is NULL", name);
     if (!im->data) return fail(PANO_ERR_INVALID_ARG, "%s->data is NULL", name);
@@ -89,7 +93,8 @@ pano_status check_params(const pano_flow_params* p) {
         return fail(PANO_ERR_INVALID_ARG, "lambda must be finite and >= 0");
     if (!(p->soft_sharpness == p->soft_sharpness) || !(p->flow_mag_coef == p->flow_mag_coef))
         return fail(PANO_ERR_INVALID_ARG, "softmax parameters must not be NaN");
-    if (p->pyr_dtype != PANO_F32) return fail(PANO_ERR_UNSUPPORTED, "pyramid dtype %d (only PANO_F32)", p->pyr_dtype);
+    if (p->pyr_dtype != PANO_F32 && p->pyr_dtype != PANO_BF16 && p->pyr_dtype != PANO_F16)
+        return fail(PANO_ERR_INVALID_ARG, "pyramid dtype %d (PANO_F32, PANO_BF16 or PANO_F16)", p->pyr_dtype);
     return PANO_OK;
 }
 
@@ -242,9 +247,9 @@ void pair_planes(const pano_flow_ctx* c, const pano_image* L, const pano_image* 
             pp->plane[si][l] = c->pyr[si][l];
             pp->pitch[si][l] = c->lev_pitch[l];
         }
-        if (img[si]->dtype == PANO_F32 && img[si]->c == 1) {
-            // a one-channel float strip is its own luma
-            pp->plane[si][0] = static_cast<const float*>(img[si]->data);
+        if (img[si]->dtype == PANO_F32 && img[si]->c == 1 && c->p.pyr_dtype == PANO_F32) {
+            // a one-channel float strip is its own luma (float32 pyramids only)
+            pp->plane[si][0] = img[si]->data;
             pp->pitch[si][0] = (int)(img[si]->pitch_bytes / sizeof(float));
         } else {
             LumaArgs& la = pp->luma;
@@ -254,6 +259,7 @@ void pair_planes(const pano_flow_ctx* c, const pano_image* L, const pano_image* 
             la.count++;
         }
     }
+    pp->luma.pyr = pyr_type(c->p.pyr_dtype);
 }
 
 cudaError_t launch_pair_pyramid(pano_flow_ctx* c, const PairPlanes& pp, cudaStream_t s) {
@@ -276,6 +282,7 @@ cudaError_t launch_pair_pyramid(pano_flow_ctx* c, const PairPlanes& pp, cudaStre
         pa.h[0] = pa.h[1] = pp.hs[l - 1];
         pa.w[0] = pa.w[1] = pp.ws[l - 1];
         pa.count = 2;
+        pa.pyr = pyr_type(c->p.pyr_dtype);
         int t = trace_begin(c->tr, PANO_TRACE_PYR_DOWN, l, s);
         if ((e = launch_pyr_down(pa, s)) != cudaSuccess) return e;
         trace_end(c->tr, t, s);
@@ -310,6 +317,7 @@ void pair_lk_args(const pano_flow_ctx* c, const PairPlanes& pp, int l, float* fl
     ka->lambda = c->p.lambda;
     ka->tile_w = c->tile_w;
     ka->tile_h = c->tile_h;
+    ka->pyr = pyr_type(c->p.pyr_dtype);
 }
 
 }  // namespace pano
@@ -368,7 +376,7 @@ pano_status pano_flow_create(const pano_flow_params* p, int max_h, int max_w, in
     for (int s = 0; s < 2; ++s)
         for (int l = 0; l < c->nlev; ++l) {
             off[0][s][l] = total;
-            total += align_up((size_t)c->lev_pitch[l] * c->lev_h[l] * sizeof(float), 256);
+            total += align_up((size_t)c->lev_pitch[l] * c->lev_h[l] * (size_t)elem_size(p->pyr_dtype), 256);
         }
     for (int d = 0; d < 2; ++d)
         for (int l = 1; l < c->nlev; ++l) {
@@ -384,7 +392,7 @@ pano_status pano_flow_create(const pano_flow_params* p, int max_h, int max_w, in
     c->buf_bytes = total;
     char* b = static_cast<char*>(c->buf);
     for (int s = 0; s < 2; ++s)
-        for (int l = 0; l < c->nlev; ++l) c->pyr[s][l] = reinterpret_cast<float*>(b + off[0][s][l]);
+        for (int l = 0; l < c->nlev; ++l) c->pyr[s][l] = b + off[0][s][l];
     for (int d = 0; d < 2; ++d)
         for (int l = 1; l < c->nlev; ++l) c->flw[d][l] = reinterpret_cast<float*>(b + off[1][d][l]);
     *out = c;

@@ -2,12 +2,35 @@
 // the optical-flow blend (Section III-C of the paper). Not a public header.
 #pragma once
 
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace pano {
 
 constexpr int kMaxLevels = 12;
+
+// Storage type of the pyramid planes. Arithmetic is FP32 throughout; a
+// 16-bit plane is widened on load and rounded to nearest even on store.
+enum PyrType : int { kPyrF32 = 0, kPyrBF16 = 1, kPyrF16 = 2 };
+
+__device__ __forceinline__ float to_f32(float v) { return v; }
+__device__ __forceinline__ float to_f32(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f32(__half v) { return __half2float(v); }
+
+template <class Ts>
+__device__ __forceinline__ Ts from_f32(float v);
+template <>
+__device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+// Read-only load of one stored element, widened to FP32.
+template <class Ts>
+__device__ __forceinline__ float ld_f32(const Ts* p) { return to_f32(__ldg(p)); }
 
 // A float32 plane in device memory: rows of `pitch` elements.
 struct Plane {
@@ -54,11 +77,12 @@ __device__ __forceinline__ float bilinear_mix(const Taps& t, float i00, float i1
     return fmaf(t.ay, bot - top, top);
 }
 
-__device__ __forceinline__ float sample_plane(const float* __restrict__ img, int pitch, int w, int h,
+template <class Ts>
+__device__ __forceinline__ float sample_plane(const Ts* __restrict__ img, int pitch, int w, int h,
                                               int qx, int qy, float ox, float oy) {
     Taps t = bilinear_taps(qx, qy, ox, oy, w, h, pitch, 1);
-    return bilinear_mix(t, __ldg(img + t.o00), __ldg(img + t.o10), __ldg(img + t.o01),
-                        __ldg(img + t.o11));
+    return bilinear_mix(t, ld_f32(img + t.o00), ld_f32(img + t.o10), ld_f32(img + t.o01),
+                        ld_f32(img + t.o11));
 }
 
 // ---------------------------------------------------------------------------
@@ -80,27 +104,29 @@ constexpr int kMaxPlanes = 2 * kMaxBatch;
 // it in place).
 struct LumaArgs {
     ImageDesc in[kMaxPlanes];
-    float* out[kMaxPlanes];
-    int out_pitch[kMaxPlanes];
+    void* out[kMaxPlanes];          // planes of type pyr
+    int out_pitch[kMaxPlanes];      // elements
     int count;
+    int pyr;                        // PyrType of the output planes
 };
 
 // One REDUCE step of up to kMaxPlanes planes of any sizes in one launch.
 struct PyrDownArgs {
-    const float* src[kMaxPlanes];
-    float* dst[kMaxPlanes];
-    int src_pitch[kMaxPlanes], dst_pitch[kMaxPlanes];
+    const void* src[kMaxPlanes];    // planes of type pyr
+    void* dst[kMaxPlanes];
+    int src_pitch[kMaxPlanes], dst_pitch[kMaxPlanes];  // elements
     int h[kMaxPlanes], w[kMaxPlanes];  // source sizes
     int count;
+    int pyr;                        // PyrType of every plane
 };
 
 // One pyramid level of Lucas-Kanade in up to two directions (blockIdx.z).
 struct LkDir {
-    const float* T;   // template level
-    const float* J;   // target level
+    const void* T;    // template level (PyrType of LkArgs::pyr)
+    const void* J;    // target level
     const float* uin; // starting / coarse flow (float2 elements), may be null
     float* uout;      // result (float2 elements)
-    int pitchT, pitchJ;  // in floats
+    int pitchT, pitchJ;  // in elements
     int uin_pitch;    // in float2 elements
     int uout_pitch;   // in float2 elements
 };
@@ -114,6 +140,7 @@ struct LkArgs {
     float lambda;
     int tile_w, tile_h;  // tiled kernel
     int seg_rows;        // streamed kernel: segment height (0 = automatic)
+    int pyr;             // PyrType of T and J
 };
 
 // The same pyramid level of several strip pairs in one launch (all share

@@ -23,9 +23,9 @@ struct pano_flow_ctx {
     int device;
     int nlev;
     int lev_h[pano::kMaxLevels], lev_w[pano::kMaxLevels];  // level sizes at the maximum strip size
-    int lev_pitch[pano::kMaxLevels];                 // floats
+    int lev_pitch[pano::kMaxLevels];                 // elements
     int flow_pitch[pano::kMaxLevels];                // float2 elements
-    float* pyr[2][pano::kMaxLevels];                 // luma pyramids of L and R
+    void* pyr[2][pano::kMaxLevels];                  // luma pyramids of L and R (pyr_dtype elements)
     float* flw[2][pano::kMaxLevels];                 // flows of levels >= 1, per direction
     void* buf;
     size_t buf_bytes;
@@ -39,7 +39,7 @@ namespace pano {
 // Plane pointers and pitches of every pyramid level of both strips of one
 // call (level 0 of a one-channel float strip is the strip itself).
 struct PairPlanes {
-    const float* plane[2][kMaxLevels];
+    const void* plane[2][kMaxLevels];  // PyrType of the context
     int pitch[2][kMaxLevels];
     int hs[kMaxLevels], ws[kMaxLevels];
     LumaArgs luma;  // level-0 conversions needed (count may be 0)
@@ -64,6 +64,8 @@ pano_status check_same(const pano_image* a, const pano_image* b, const char* na,
 pano_status check_flow(const void* f, const char* name);
 pano_status check_params(const pano_flow_params* p);
 bool overlaps(const void* a, size_t na, const void* b, size_t nb);
+int elem_size(int dtype);           // bytes of one element of a pano_dtype
+int pyr_type(int pyr_dtype);        // PyrType of a pano_dtype
 size_t align_up(size_t v, size_t a);
 ImageDesc desc(const pano_image* im);
 // largest tile of the LK tile kernel that fits max_smem bytes

@@ -46,8 +46,9 @@ __device__ __forceinline__ float2 start_flow(const LkArgs& a, const LkDir& D, in
     return make_float2(2.f * fmaf(fy, bx - tx, tx), 2.f * fmaf(fy, by - ty, ty));
 }
 
-// One output tile (bx, by) of direction `dir` of one level.
-template <int RAD>
+// One output tile (bx, by) of direction `dir` of one level; T and J stored
+// as Ts.
+template <int RAD, class Ts>
 __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, int by, float4* smem4) {
     const LkDir& D = a.dir[dir];
     const int K = a.iters;
@@ -63,8 +64,8 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
     const int ox = bx * a.tile_w - halo, oy = by * a.tile_h - halo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int w = a.w, h = a.h, pitchT = D.pitchT, pitchJ = D.pitchJ;
-    const float* __restrict__ T = D.T;
-    const float* __restrict__ J = D.J;
+    const Ts* __restrict__ T = static_cast<const Ts*>(D.T);
+    const Ts* __restrict__ J = static_cast<const Ts*>(D.J);
 
     // Phase 0: template, its gradient and the starting flow on the region.
     for (int ry = warp; ry < RH; ry += nwarps) {
@@ -74,11 +75,11 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
             float t = 0.f;
             float2 g = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f);
             if (x >= 0 && x < w && y >= 0 && y < h) {
-                const float* row = T + (long long)y * pitchT;
-                t = __ldg(row + x);
-                g.x = 0.5f * (__ldg(row + min(x + 1, w - 1)) - __ldg(row + max(x - 1, 0)));
-                g.y = 0.5f * (__ldg(T + (long long)min(y + 1, h - 1) * pitchT + x) -
-                              __ldg(T + (long long)max(y - 1, 0) * pitchT + x));
+                const Ts* row = T + (long long)y * pitchT;
+                t = ld_f32(row + x);
+                g.x = 0.5f * (ld_f32(row + min(x + 1, w - 1)) - ld_f32(row + max(x - 1, 0)));
+                g.y = 0.5f * (ld_f32(T + (long long)min(y + 1, h - 1) * pitchT + x) -
+                              ld_f32(T + (long long)max(y - 1, 0) * pitchT + x));
                 u = start_flow(a, D, x, y);
             }
             const int i = ry * RW + rx;
@@ -195,45 +196,78 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
     }
 }
 
-template <int RAD>
+template <int RAD, class Ts>
 __global__ void __launch_bounds__(kLkThreads) lk_level_kernel(const __grid_constant__ LkArgs a) {
     extern __shared__ float4 smem4[];
-    lk_tile_item<RAD>(a, blockIdx.z, blockIdx.x, blockIdx.y, smem4);
+    lk_tile_item<RAD, Ts>(a, blockIdx.z, blockIdx.x, blockIdx.y, smem4);
 }
 
 // The same level of several strip pairs: blockIdx.z = 2 * pair + direction,
 // the x/y grid covers the largest pair and tiles beyond a smaller pair exit.
-template <int RAD>
+template <int RAD, class Ts>
 __global__ void __launch_bounds__(kLkThreads) lk_level_batch_kernel(const __grid_constant__ LkBatch b) {
     extern __shared__ float4 smem4[];
     const LkArgs& a = b.pair[blockIdx.z >> 1];
     if ((int)blockIdx.x * a.tile_w >= a.w || (int)blockIdx.y * a.tile_h >= a.h) return;
-    lk_tile_item<RAD>(a, blockIdx.z & 1, blockIdx.x, blockIdx.y, smem4);
+    lk_tile_item<RAD, Ts>(a, blockIdx.z & 1, blockIdx.x, blockIdx.y, smem4);
 }
 
-template <int RAD>
+template <int RAD, class Ts>
 cudaError_t launch_rad(const LkArgs& a, int ndirs, cudaStream_t s) {
     size_t smem = lk_smem_bytes(a.tile_w, a.tile_h, a.iters, a.radius);
     dim3 grid((a.w + a.tile_w - 1) / a.tile_w, (a.h + a.tile_h - 1) / a.tile_h, ndirs);
-    lk_level_kernel<RAD><<<grid, kLkThreads, smem, s>>>(a);
+    lk_level_kernel<RAD, Ts><<<grid, kLkThreads, smem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int RAD>
+template <int RAD, class Ts>
 cudaError_t launch_rad_batch(const LkBatch& b, cudaStream_t s) {
     const LkArgs& a0 = b.pair[0];
     size_t smem = lk_smem_bytes(a0.tile_w, a0.tile_h, a0.iters, a0.radius);
     int gx = 0, gy = 0;
     for (int p = 0; p < b.n; ++p) {
         const LkArgs& a = b.pair[p];
-        if (a.tile_w != a0.tile_w || a.tile_h != a0.tile_h || a.iters != a0.iters || a.radius != a0.radius)
+        if (a.tile_w != a0.tile_w || a.tile_h != a0.tile_h || a.iters != a0.iters || a.radius != a0.radius ||
+            a.pyr != a0.pyr)
             return cudaErrorInvalidValue;
         gx = max(gx, (a.w + a.tile_w - 1) / a.tile_w);
         gy = max(gy, (a.h + a.tile_h - 1) / a.tile_h);
     }
     dim3 grid(gx, gy, 2 * b.n);
-    lk_level_batch_kernel<RAD><<<grid, kLkThreads, smem, s>>>(b);
+    lk_level_batch_kernel<RAD, Ts><<<grid, kLkThreads, smem, s>>>(b);
     return cudaGetLastError();
+}
+
+template <class Ts>
+cudaError_t launch_tile_t(const LkArgs& a, int ndirs, cudaStream_t s) {
+    switch (a.radius) {
+        case 1: return launch_rad<1, Ts>(a, ndirs, s);
+        case 2: return launch_rad<2, Ts>(a, ndirs, s);
+        case 3: return launch_rad<3, Ts>(a, ndirs, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Ts>
+cudaError_t launch_tile_batch_t(const LkBatch& b, cudaStream_t s) {
+    switch (b.pair[0].radius) {
+        case 1: return launch_rad_batch<1, Ts>(b, s);
+        case 2: return launch_rad_batch<2, Ts>(b, s);
+        case 3: return launch_rad_batch<3, Ts>(b, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Ts>
+cudaError_t prepare_tile_t(int max_smem_bytes) {
+    const void* fns[] = {(const void*)lk_level_kernel<1, Ts>,       (const void*)lk_level_kernel<2, Ts>,
+                         (const void*)lk_level_kernel<3, Ts>,       (const void*)lk_level_batch_kernel<1, Ts>,
+                         (const void*)lk_level_batch_kernel<2, Ts>, (const void*)lk_level_batch_kernel<3, Ts>};
+    for (const void* f : fns) {
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace
@@ -247,13 +281,9 @@ size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius) {
 cudaError_t lk_prepare(int max_smem_bytes) {
     cudaError_t e;
     if ((e = lk_stream_prepare(max_smem_bytes)) != cudaSuccess) return e;
-    const void* fns[] = {(const void*)lk_level_kernel<1>,       (const void*)lk_level_kernel<2>,
-                         (const void*)lk_level_kernel<3>,       (const void*)lk_level_batch_kernel<1>,
-                         (const void*)lk_level_batch_kernel<2>, (const void*)lk_level_batch_kernel<3>};
-    for (const void* f : fns)
-        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes)) != cudaSuccess)
-            return e;
-    return cudaSuccess;
+    if ((e = prepare_tile_t<float>(max_smem_bytes)) != cudaSuccess) return e;
+    if ((e = prepare_tile_t<__nv_bfloat16>(max_smem_bytes)) != cudaSuccess) return e;
+    return prepare_tile_t<__half>(max_smem_bytes);
 }
 
 cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s) {
@@ -266,19 +296,19 @@ cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s) {
 
 cudaError_t launch_lk_tile_batch(const LkBatch& b, cudaStream_t s) {
     if (b.n < 1 || b.n > kMaxBatch) return cudaErrorInvalidValue;
-    switch (b.pair[0].radius) {
-        case 1: return launch_rad_batch<1>(b, s);
-        case 2: return launch_rad_batch<2>(b, s);
-        case 3: return launch_rad_batch<3>(b, s);
+    switch (b.pair[0].pyr) {
+        case kPyrF32: return launch_tile_batch_t<float>(b, s);
+        case kPyrBF16: return launch_tile_batch_t<__nv_bfloat16>(b, s);
+        case kPyrF16: return launch_tile_batch_t<__half>(b, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_lk_tile(const LkArgs& a, int ndirs, cudaStream_t s) {
-    switch (a.radius) {
-        case 1: return launch_rad<1>(a, ndirs, s);
-        case 2: return launch_rad<2>(a, ndirs, s);
-        case 3: return launch_rad<3>(a, ndirs, s);
+    switch (a.pyr) {
+        case kPyrF32: return launch_tile_t<float>(a, ndirs, s);
+        case kPyrBF16: return launch_tile_t<__nv_bfloat16>(a, ndirs, s);
+        case kPyrF16: return launch_tile_t<__half>(a, ndirs, s);
         default: return cudaErrorInvalidValue;
     }
 }

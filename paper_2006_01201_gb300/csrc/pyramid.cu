@@ -4,7 +4,8 @@
 // the pyramid is the Burt-Adelson REDUCE: the binomial [1 4 6 4 1]/16
 // along y, then along x, replicate border, keeping the even rows and
 // columns (level size ceil(h/2) x ceil(w/2)). Level 0 is the BT.601 luma of
-// the unit-scaled strip.
+// the unit-scaled strip. Levels are stored as float32, bfloat16 or binary16
+// (rounded to nearest even); every sum is formed in FP32.
 #include "common.cuh"
 
 namespace pano {
@@ -31,15 +32,39 @@ __device__ __forceinline__ float luma_at(const ImageDesc& in, const unsigned cha
     return r[x];
 }
 
+// Four consecutive outputs: one 16-byte store for float32 rows, one 8-byte
+// store for 16-bit rows, when the address allows it.
+__device__ __forceinline__ void store4(float* o, const float (&v)[4]) {
+    if ((((uintptr_t)o) & 15) == 0) {
+        *reinterpret_cast<float4*>(o) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = v[k];
+    }
+}
+template <class To>
+__device__ __forceinline__ void store4(To* o, const float (&v)[4]) {
+    To q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) q[k] = from_f32<To>(v[k]);
+    if ((((uintptr_t)o) & 7) == 0) {
+        *reinterpret_cast<uint2*>(o) = *reinterpret_cast<const uint2*>(q);
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = q[k];
+    }
+}
+
+template <class To>
 __global__ void __launch_bounds__(256) luma_kernel(const __grid_constant__ LumaArgs a) {
     const ImageDesc& in = a.in[blockIdx.z];
-    float* out = a.out[blockIdx.z];
+    To* out = static_cast<To*>(a.out[blockIdx.z]);
     const int out_pitch = a.out_pitch[blockIdx.z];
     const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y;
     if (x >= in.w || y >= in.h) return;
     const unsigned char* row = static_cast<const unsigned char*>(in.data) + (long long)y * in.pitch_bytes;
-    float* orow = out + (long long)y * out_pitch;
+    To* orow = out + (long long)y * out_pitch;
     if (x + 4 <= in.w && in.dtype == 0 && in.c == 3 && ((((uintptr_t)row) + 3 * x) & 3) == 0) {
         // 12 aligned bytes = 4 RGB pixels
         const uint32_t* p = reinterpret_cast<const uint32_t*>(row + 3 * x);
@@ -51,16 +76,11 @@ __global__ void __launch_bounds__(256) luma_kernel(const __grid_constant__ LumaA
 #pragma unroll
         for (int k = 0; k < 4; ++k)
             v[k] = (0.299f * (float)b[3 * k] + 0.587f * (float)b[3 * k + 1] + 0.114f * (float)b[3 * k + 2]) * kInv255;
-        if ((((uintptr_t)(orow + x)) & 15) == 0) {
-            *reinterpret_cast<float4*>(orow + x) = make_float4(v[0], v[1], v[2], v[3]);
-        } else {
-#pragma unroll
-            for (int k = 0; k < 4; ++k) orow[x + k] = v[k];
-        }
+        store4(orow + x, v);
         return;
     }
     const int n = min(4, in.w - x);
-    for (int k = 0; k < n; ++k) orow[x + k] = luma_at(in, row, x + k);
+    for (int k = 0; k < n; ++k) orow[x + k] = from_f32<To>(luma_at(in, row, x + k));
 }
 
 // ---------------------------------------------------------------------------
@@ -73,12 +93,13 @@ constexpr int kPdTW = 32, kPdTH = 8;
 constexpr int kPdSW = 2 * kPdTW + 3;  // source columns 2*x0-2 .. 2*(x0+31)+2
 constexpr int kPdSH = 2 * kPdTH + 3;
 
+template <class Ts>
 __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ PyrDownArgs a) {
     __shared__ float s_src[kPdSH][kPdSW + 1];
     __shared__ float s_v[kPdTH][kPdSW + 1];
     const int z = blockIdx.z;
-    const float* __restrict__ src = a.src[z];
-    float* __restrict__ dst = a.dst[z];
+    const Ts* __restrict__ src = static_cast<const Ts*>(a.src[z]);
+    Ts* __restrict__ dst = static_cast<Ts*>(a.dst[z]);
     const int src_pitch = a.src_pitch[z], dst_pitch = a.dst_pitch[z];
     const int h = a.h[z], w = a.w[z];
     const int hd = (h + 1) >> 1, wd = (w + 1) >> 1;
@@ -90,7 +111,7 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ P
         int r = i / kPdSW, c = i - r * kPdSW;
         int sy = min(max(sy0 + r, 0), h - 1);
         int sx = min(max(sx0 + c, 0), w - 1);
-        s_src[r][c] = __ldg(src + (long long)sy * src_pitch + sx);
+        s_src[r][c] = ld_f32(src + (long long)sy * src_pitch + sx);
     }
     __syncthreads();
     const float k0 = 1.0f / 16, k1 = 4.0f / 16, k2 = 6.0f / 16;
@@ -106,7 +127,7 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ P
         int c = 2 * threadIdx.x + 2;
         const float* v = s_v[threadIdx.y];
         dst[(long long)yd * dst_pitch + xd] =
-            k0 * v[c - 2] + k1 * v[c - 1] + k2 * v[c] + k1 * v[c + 1] + k0 * v[c + 2];
+            from_f32<Ts>(k0 * v[c - 2] + k1 * v[c - 1] + k2 * v[c] + k1 * v[c + 1] + k0 * v[c + 2]);
     }
 }
 
@@ -121,7 +142,12 @@ cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s) {
     }
     dim3 block(64);
     dim3 grid((w + 4 * 64 - 1) / (4 * 64), h, a.count);
-    luma_kernel<<<grid, block, 0, s>>>(a);
+    switch (a.pyr) {
+        case kPyrF32: luma_kernel<float><<<grid, block, 0, s>>>(a); break;
+        case kPyrBF16: luma_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(a); break;
+        case kPyrF16: luma_kernel<__half><<<grid, block, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
@@ -134,7 +160,12 @@ cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s) {
     }
     dim3 block(kPdTW, kPdTH);
     dim3 grid((wd + kPdTW - 1) / kPdTW, (hd + kPdTH - 1) / kPdTH, a.count);
-    pyr_down_kernel<<<grid, block, 0, s>>>(a);
+    switch (a.pyr) {
+        case kPyrF32: pyr_down_kernel<float><<<grid, block, 0, s>>>(a); break;
+        case kPyrBF16: pyr_down_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(a); break;
+        case kPyrF16: pyr_down_kernel<__half><<<grid, block, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -53,9 +53,9 @@ struct pano_rig {
     int def_tile_w, def_tile_h;    // default tile of the tiled kernel
     int hs[kMaxLevels];            // level heights (shared by all pairs)
     int ws[kMaxBatch][kMaxLevels]; // level widths per pair
-    int lev_pitch[kMaxBatch][kMaxLevels];   // floats
+    int lev_pitch[kMaxBatch][kMaxLevels];   // elements of the pyramid dtype
     int flow_pitch[kMaxBatch][kMaxLevels];  // float2 elements
-    float* pyr[kMaxBatch][2][kMaxLevels];   // luma pyramids of L and R
+    void* pyr[kMaxBatch][2][kMaxLevels];    // luma pyramids of L and R (pyr_dtype elements)
     float* flw[kMaxBatch][2][kMaxLevels];   // flows per direction; level 0 = the rig's own output flows
     unsigned* counters;                     // work counters of the persistent launches, one per level
     void* buf;
@@ -143,13 +143,18 @@ pano_status check_device(const pano_rig* r) {
     return PANO_OK;
 }
 
-// Level-0 plane of strip side `s` (0 = L, 1 = R) of pair k: a one-channel
-// float strip is its own luma.
-const float* level0(const pano_rig* r, const RunCall& c, int k, int s, int* pitch) {
+// Whether strip side `s` of pair k is its own level 0: a one-channel float
+// strip with float32 pyramids.
+bool own_level0(const pano_rig* r, const pano_image& im) {
+    return im.dtype == PANO_F32 && im.c == 1 && r->p.pyr_dtype == PANO_F32;
+}
+
+// Level-0 plane of strip side `s` (0 = L, 1 = R) of pair k.
+const void* level0(const pano_rig* r, const RunCall& c, int k, int s, int* pitch) {
     const pano_image& im = s == 0 ? c.L[k] : c.R[k];
-    if (im.dtype == PANO_F32 && im.c == 1) {
+    if (own_level0(r, im)) {
         *pitch = (int)(im.pitch_bytes / sizeof(float));
-        return static_cast<const float*>(im.data);
+        return im.data;
     }
     *pitch = r->lev_pitch[k][0];
     return r->pyr[k][s][0];
@@ -162,8 +167,8 @@ LkArgs pair_level_args(const pano_rig* r, const RunCall& c, int k, int l, const 
     for (int d = 0; d < 2; ++d) {
         // direction 0: FlowLtoR (template L, target R); 1: FlowRtoL
         int pt = r->lev_pitch[k][l], pj = r->lev_pitch[k][l];
-        const float* T = r->pyr[k][d][l];
-        const float* J = r->pyr[k][1 - d][l];
+        const void* T = r->pyr[k][d][l];
+        const void* J = r->pyr[k][1 - d][l];
         if (l == 0) {
             T = level0(r, c, k, d, &pt);
             J = level0(r, c, k, 1 - d, &pj);
@@ -189,6 +194,7 @@ LkArgs pair_level_args(const pano_rig* r, const RunCall& c, int k, int l, const 
     a.tile_w = t.tile_w ? t.tile_w : r->def_tile_w;
     a.tile_h = t.tile_h ? t.tile_h : r->def_tile_h;
     a.seg_rows = t.seg_rows;
+    a.pyr = pyr_type(r->p.pyr_dtype);
     return a;
 }
 
@@ -240,12 +246,13 @@ cudaError_t enqueue_all(pano_rig* r, const RunCall& c, cudaStream_t s, bool trac
     for (int k = 0; k < n; ++k)
         for (int si = 0; si < 2; ++si) {
             const pano_image& im = si == 0 ? c.L[k] : c.R[k];
-            if (im.dtype == PANO_F32 && im.c == 1) continue;
+            if (own_level0(r, im)) continue;
             la.in[la.count] = desc(&im);
             la.out[la.count] = r->pyr[k][si][0];
             la.out_pitch[la.count] = r->lev_pitch[k][0];
             la.count++;
         }
+    la.pyr = pyr_type(r->p.pyr_dtype);
     if (la.count) {
         int slot = trace ? trace_begin(r->tr, PANO_TRACE_LUMA, 0, s) : -1;
         if ((e = launch_luma(la, s)) != cudaSuccess) return e;
@@ -259,7 +266,7 @@ cudaError_t enqueue_all(pano_rig* r, const RunCall& c, cudaStream_t s, bool trac
         for (int k = 0; k < n; ++k)
             for (int si = 0; si < 2; ++si) {
                 int sp = r->lev_pitch[k][l - 1];
-                const float* src = l == 1 ? level0(r, c, k, si, &sp) : r->pyr[k][si][l - 1];
+                const void* src = l == 1 ? level0(r, c, k, si, &sp) : r->pyr[k][si][l - 1];
                 pa.src[pa.count] = src;
                 pa.src_pitch[pa.count] = sp;
                 pa.dst[pa.count] = r->pyr[k][si][l];
@@ -268,6 +275,7 @@ cudaError_t enqueue_all(pano_rig* r, const RunCall& c, cudaStream_t s, bool trac
                 pa.w[pa.count] = r->ws[k][l - 1];
                 pa.count++;
             }
+        pa.pyr = pyr_type(r->p.pyr_dtype);
         int slot = trace ? trace_begin(r->tr, PANO_TRACE_PYR_DOWN, l, s) : -1;
         if ((e = launch_pyr_down(pa, s)) != cudaSuccess) return e;
         if (slot >= 0) trace_end(r->tr, slot, s);
@@ -441,7 +449,7 @@ pano_status pano_rig_create(const pano_flow_params* p, const pano_rig_desc* d, p
             r->flow_pitch[k][l] = l == 0 ? d->w[k] : (int)align_up(r->ws[k][l], 16);
             for (int s = 0; s < 2; ++s) {
                 offs.push_back(total);
-                total += align_up((size_t)r->lev_pitch[k][l] * r->hs[l] * sizeof(float), 256);
+                total += align_up((size_t)r->lev_pitch[k][l] * r->hs[l] * (size_t)elem_size(p->pyr_dtype), 256);
             }
             for (int s = 0; s < 2; ++s) {
                 offs.push_back(total);
@@ -461,7 +469,7 @@ pano_status pano_rig_create(const pano_flow_params* p, const pano_rig_desc* d, p
     size_t i = 0;
     for (int k = 0; k < n; ++k)
         for (int l = 0; l < r->nlev; ++l) {
-            for (int s = 0; s < 2; ++s) r->pyr[k][s][l] = reinterpret_cast<float*>(b + offs[i++]);
+            for (int s = 0; s < 2; ++s) r->pyr[k][s][l] = b + offs[i++];
             for (int s = 0; s < 2; ++s) r->flw[k][s][l] = reinterpret_cast<float*>(b + offs[i++]);
         }
     if ((e = cudaStreamCreateWithFlags(&r->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {

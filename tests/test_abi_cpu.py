@@ -64,8 +64,9 @@ def test_create_rejects_bad_arguments_before_any_device_call(lib):
             binding.PANO_ERR_INVALID_ARG, (field, value)
     q = binding.PanoParams()
     lib.pano_flow_params_default(ctypes.byref(q))
-    q.pyr_dtype = binding.PANO_BF16
-    assert lib.pano_flow_create(ctypes.byref(q), 10, 10, 1, ctypes.byref(out)) == binding.PANO_ERR_UNSUPPORTED
+    for bad in (binding.PANO_U8, 7):
+        q.pyr_dtype = bad
+        assert lib.pano_flow_create(ctypes.byref(q), 10, 10, 1, ctypes.byref(out)) == binding.PANO_ERR_INVALID_ARG
     assert lib.pano_flow_create(ctypes.byref(p), 0, 10, 1, ctypes.byref(out)) == binding.PANO_ERR_INVALID_ARG
     assert lib.pano_flow_create(ctypes.byref(p), 10, 10, 2, ctypes.byref(out)) == binding.PANO_ERR_INVALID_ARG
 

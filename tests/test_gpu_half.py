@@ -1,0 +1,112 @@
+"""16-bit pyramid storage (pano_flow_params.pyr_dtype = PANO_BF16 / PANO_F16)
+against the oracle with the same storage rounding, and against the exact
+FP64 oracle and the float32 GPU path.
+
+Parity bar: the GPU rounds levels it computed in FP32, the oracle levels it
+computed in FP64, so a value within FP32 rounding of a tie between two
+16-bit neighbours can land one storage ulp apart (rare); flows therefore
+match the storage-matched oracle to a mean endpoint error of 1e-3 px, and
+the blended u8 strips to 1 LSB. Against the exact oracle the end-to-end
+bound of the float32 path applies: mean endpoint error <= 0.05 px."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import oracle  # noqa: E402
+import synth  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+from paper_2006_01201_gb300 import binding  # noqa: E402
+from paper_2006_01201_gb300 import build as gpu_build  # noqa: E402
+
+DEV = torch.device("cuda:0")
+FORMATS = [(binding.PANO_BF16, oracle.FMT_BF16), (binding.PANO_F16, oracle.FMT_F16)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    gpu_build.build()
+    binding.load_library()
+
+
+def cuda(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def epe(a, b):
+    return np.hypot(*(a - b).transpose(2, 0, 1))
+
+
+def gpu_stitch(pair, levels, pyr_dtype):
+    h, w = pair.L.shape[:2]
+    c = pair.L.shape[2] if pair.L.ndim == 3 else 1
+    with binding.FlowContext(binding.Params(levels=levels, pyr_dtype=pyr_dtype), h, w, c) as ctx:
+        lr, rl, F = ctx.stitch_pair(cuda(pair.L), cuda(pair.R))
+        torch.cuda.synchronize()
+        return lr.cpu().numpy(), rl.cpu().numpy(), F.cpu().numpy()
+
+
+@pytest.mark.parametrize("dt,fmt", FORMATS)
+@pytest.mark.parametrize("kind", ["gray_f32", "rgb_u8"])
+def test_half_pyramids_match_storage_matched_oracle(dt, fmt, kind):
+    if kind == "gray_f32":
+        pair, levels = synth.pair_small_gray(), 4
+    else:
+        pair, levels = synth.pair_fullres_rgb(seed=3, h=480, w=360, dmax=8.0, levels=4), 4
+    lr, rl, F = gpu_stitch(pair, levels, dt)
+    olr, orl = oracle.flow_pair(pair.L, pair.R, oracle.Params(levels=levels, pyr_fmt=fmt))
+    for g, o in ((lr, olr), (rl, orl)):
+        e = epe(g, o)
+        assert e.mean() <= 1e-3, e.mean()
+    Fo = oracle.blend(pair.L, pair.R, olr, orl, oracle.Params(levels=levels))
+    if pair.L.dtype == np.uint8:
+        d = np.abs(F.astype(int) - oracle.quantize_u8(Fo).astype(int))
+        assert np.percentile(d, 99.9) <= 1
+    else:
+        d = np.abs(F - Fo)
+        assert np.percentile(d, 99.9) <= 1.0 / 255
+    # against the exact oracle: the end-to-end bound of the float32 path
+    xlr, xrl = oracle.flow_pair(pair.L, pair.R, oracle.Params(levels=levels))
+    assert epe(lr, xlr).mean() <= 0.05 and epe(rl, xrl).mean() <= 0.05
+
+
+@pytest.mark.parametrize("dt", [binding.PANO_BF16, binding.PANO_F16])
+def test_half_identical_strips_give_zero_flow_and_swap_is_exact(dt):
+    pair = synth.pair_fullres_rgb(seed=4, h=256, w=200, dmax=6.0, levels=3)
+    with binding.FlowContext(binding.Params(levels=3, pyr_dtype=dt), 256, 200, 3) as ctx:
+        L, R = cuda(pair.L), cuda(pair.R)
+        z1, z2 = ctx.flow_pair(L, L)
+        lr, rl = ctx.flow_pair(L, R)
+        rl2, lr2 = ctx.flow_pair(R, L)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(z1) == 0 and torch.count_nonzero(z2) == 0
+        assert torch.equal(lr, lr2) and torch.equal(rl, rl2)
+
+
+def test_half_rig_equals_half_single_pair_path():
+    widths = (240, 300)
+    pairs = [synth.pair_fullres_rgb(seed=60 + k, h=400, w=w, dmax=6.0, levels=4) for k, w in enumerate(widths)]
+    prm = binding.Params(levels=4, pyr_dtype=binding.PANO_BF16)
+    with binding.FlowContext(prm, 400, 300, 3) as ctx:
+        ref = [ctx.flow_pair(cuda(p.L), cuda(p.R)) for p in pairs]
+        torch.cuda.synchronize()
+    with binding.Rig(prm, 400, widths, canvas_hw=(400, 600), canvas_x0=(0, 300)) as rig:
+        rig.run([cuda(p.L) for p in pairs], [cuda(p.R) for p in pairs], use_graph=True)
+        torch.cuda.synchronize()
+        for k in range(2):
+            a, b = rig.flows(k)
+            assert torch.equal(a, ref[k][0]) and torch.equal(b, ref[k][1])
+
+
+def test_half_differs_from_float_only_by_storage_rounding():
+    pair = synth.pair_fullres_rgb(seed=5, h=600, w=400, dmax=8.0, levels=4)
+    f32 = gpu_stitch(pair, 4, binding.PANO_F32)
+    for dt, bound in ((binding.PANO_F16, 0.01), (binding.PANO_BF16, 0.05)):
+        half = gpu_stitch(pair, 4, dt)
+        assert 0 < epe(half[0], f32[0]).mean() <= bound
+        assert 0 < epe(half[1], f32[1]).mean() <= bound
