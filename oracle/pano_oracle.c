@@ -407,6 +407,9 @@ void oracle_flow_pair(const double* YL, const double* YR, int h, int w, int leve
  * between pixel centres from (i, j) to any Area1 / Area2 pixel. Cost is
  * O(N^2): tiny canvases only.
  *   Blend = 0 in Area1, 1 in Area2, Lmin / (Lmin + Rmin) in Area3, 0.5 else.
+ * Eq. (1) is undefined when the canvas has no Area1 (or no Area2) pixel; the
+ * reading used is its limit as that area moves infinitely far away: no
+ * Area1 gives Blend = 1 in Area3, no Area2 gives 0, neither gives 0.5.
  * ------------------------------------------------------------------------- */
 void oracle_blend_coeff(const unsigned char* label, int h, int w, double* blend)
 {
@@ -426,7 +429,10 @@ void oracle_blend_coeff(const unsigned char* label, int h, int w, double* blend)
                         if (b == 1 && d < lmin) lmin = d;
                         if (b == 2 && d < rmin) rmin = d;
                     }
-                v = lmin / (lmin + rmin);
+                if (isinf(lmin) && isinf(rmin)) v = 0.5;
+                else if (isinf(lmin)) v = 1.0;
+                else if (isinf(rmin)) v = 0.0;
+                else v = lmin / (lmin + rmin);
             } else v = 0.5;
             PIX(blend, w, i, j) = v;
         }

@@ -323,6 +323,19 @@ def test_blend_coeff_matches_scipy_edt_on_random_masks():
     np.testing.assert_allclose(oracle.blend_coeff(label), expect, rtol=0, atol=1e-14)
 
 
+def test_blend_coeff_with_a_missing_area_is_the_limit_of_eq1():
+    # no Area1 pixel: Lmin -> infinity, Lmin / (Lmin + Rmin) -> 1; no Area2: -> 0
+    lab = np.full((3, 5), 3, np.uint8)
+    lab[:, -1] = 2
+    out = oracle.blend_coeff(lab)
+    assert (out[:, :-1] == 1.0).all() and (out[:, -1] == 1.0).all()
+    lab[:, -1] = 1
+    out = oracle.blend_coeff(lab)
+    assert (out[:, :-1] == 0.0).all() and (out[:, -1] == 0.0).all()
+    lab[:, -1] = 0
+    assert (oracle.blend_coeff(lab) == 0.5).all()
+
+
 @pytest.mark.parametrize("w", [1, 4, 9, 31])
 def test_blend_ramp_is_eq1_for_a_strip(w):
     # canvas: Area1 column, w overlap columns, Area2 column, 3 rows
