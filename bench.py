@@ -459,6 +459,63 @@ def half_precision_report(pkg, pair, levels, pyr_fmt, g_lr, g_rl, g_F, olr, orl,
                                      "frac_gt_1lsb": float((do > 1).mean())}}
 
 
+def run_blend_coeff(args):
+    """General-mask Eq. (1): the blending coefficient of a 4000 x 9000
+    panorama canvas with wavy seams between Area1, Area3 and Area2 and holes
+    (exact distance transform + ratio), one pano_blend_coeff per step."""
+    import numpy as np
+    import torch
+
+    import paper_2006_01201_gb300 as pkg
+    from paper_2006_01201_gb300 import binding, build as gpu_build
+
+    gpu_build.build()
+    pkg.load_library()
+    dev = torch.device("cuda", 0)
+    h, w = 4000, 9000
+    g = np.random.default_rng(8)
+    ys = np.arange(h)[:, None]
+    xs = np.arange(w)[None, :]
+    a = 0.3 * w + 0.08 * w * np.sin(2 * np.pi * ys / (0.7 * h) + g.uniform(0, 6)) + g.normal(0, 0.01 * w, (h, 1))
+    b = 0.7 * w + 0.08 * w * np.sin(2 * np.pi * ys / (0.5 * h) + g.uniform(0, 6))
+    lab = np.where(xs < a, 1, np.where(xs >= b, 2, 3)).astype(np.uint8)
+    for _ in range(6):
+        cy, cx, r = g.integers(0, h), g.integers(0, w), g.integers(1, 400)
+        lab[(ys - cy) ** 2 + (xs - cx) ** 2 <= r * r] = 0
+    label = torch.from_numpy(lab).to(dev)
+    out = torch.empty((h, w), dtype=torch.float32, device=dev)
+    scratch = torch.empty(int(binding.load_library().pano_blend_coeff_scratch_bytes(h, w)), dtype=torch.uint8,
+                          device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        binding.blend_coeff(label, out=out, scratch=scratch)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record()
+        binding.blend_coeff(label, out=out, scratch=scratch)
+        ev[k][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / args.steps
+    npx = h * w
+    alg = 5 * npx          # label read (1 B) and Blend written (4 B) once per pixel
+    peak, src = read_peaks()
+    line = {"metric": "general-mask Eq. (1) blending coefficient, canvas megapixels/sec",
+            "value": npx / (ms * 1e-3) / 1e6, "unit": "MP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i32+f32", "data": "synthetic",
+            "config": {"workload": "blend_coeff_canvas_4000x9000_wavy_seams_holes",
+                       "l2": "flushed between steps (256 MB write, untimed)",
+                       "area3_fraction": float((lab == 3).mean())},
+            "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None,
+                         "kernel": "edt_cols_kernel + edt_rows_blend_kernel", "alg_bytes_per_launch": alg,
+                         "peak_source": f"{src} hbm_gbs"}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_refine(args):
     """Differentiable-refinement workload: 1024x1024 gray f32 pair (6 px
     sinusoidal field, 5 levels). Times the energy + adjoint kernel at level 0
@@ -762,9 +819,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "refine_1024"],
+    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "refine_1024", "blend_coeff"],
                     help="pair: the 4000x1500 overlap pair (default); rig: the 8-pair 360-degree rig; "
-                         "refine_1024: the differentiable refinement")
+                         "refine_1024: the differentiable refinement; blend_coeff: general-mask Eq. (1)")
     ap.add_argument("--no-autotune", action="store_true", help="rig: keep the default tuning")
     ap.add_argument("--pyr-dtype", default="f32", choices=sorted(PYR_DTYPES),
                     help="storage of the pyramid levels (arithmetic stays FP32)")
@@ -777,6 +834,8 @@ def main(argv=None):
         return run_refine(args)
     if args.workload == "rig":
         return run_rig(args)
+    if args.workload == "blend_coeff":
+        return run_blend_coeff(args)
     return run_gpu(args)
 
 

@@ -149,6 +149,29 @@ PANO_API pano_status pano_flow_destroy(pano_flow_ctx* ctx);
 PANO_API const char* pano_last_error(const pano_flow_ctx* ctx);
 
 /* ----------------------------------------------------------------------
+ * Global blending coefficient of Eq. (1) (Section III-C-2) for overlaps of
+ * any shape. label is an h x w canvas of bytes (row pitch label_pitch):
+ * 1 = Area1 (covered by L only), 2 = Area2 (R only), 3 = Area3 (the
+ * overlap), any other value = neither. blend receives h x w float32 values
+ * (row pitch blend_pitch elements):
+ *   Blend = 0 in Area1, 1 in Area2, 0.5 in neither, and in Area3
+ *   Lmin / (Lmin + Rmin), Lmin / Rmin the Euclidean distances between pixel
+ *   centres to the nearest Area1 / Area2 pixel.
+ * With no Area1 pixel on the canvas Area3 gets 1, with no Area2 pixel 0,
+ * with neither 0.5 (the limits of Eq. 1). The distances are exact (integer
+ * distance transform); the ratio is rounded in FP32. The Blend array of a
+ * strip can be passed to pano_blend_pair.
+ * scratch: device memory of at least pano_blend_coeff_scratch_bytes(h, w)
+ * bytes (2 * 4 * h * w), 4-byte aligned; label, blend and scratch must not
+ * overlap. Sides up to 65535; the width is limited further by shared memory
+ * (8 bytes per column: 29000 columns on a GB300).
+ * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
+ * ---------------------------------------------------------------------- */
+PANO_API size_t pano_blend_coeff_scratch_bytes(int h, int w);
+PANO_API pano_status pano_blend_coeff(const unsigned char* label, int h, int w, size_t label_pitch, float* blend,
+                                      int blend_pitch, void* scratch, size_t scratch_bytes, void* cuda_stream);
+
+/* ----------------------------------------------------------------------
  * Differentiable refinement. Not a step of the paper: a build extension
  * that refines a flow by gradient steps on the energy
  *   E(u) = sum_p (J(p + u(p)) - T(p))^2

@@ -69,6 +69,8 @@ def lib():
             "oracle_flow_pair": ([_D, _D, i, i, i, i, i, d, _D, _D], None),
             "oracle_blend_coeff": ([_U8, i, i, _D], None),
             "oracle_blend_ramp": ([i, _D], None),
+            "oracle_blend_coeff_at": ([_U8, i, i, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), l, _D],
+                                      None),
             "oracle_blend": ([_D, _D, i, i, i, _D, _D, _D, d, d, _D], None),
             "oracle_blend_weights": ([i, i, _D, _D, _D, d, d, _D, _D], None),
             "oracle_quantize_u8": ([_D, l, _U8], None),
@@ -257,6 +259,19 @@ def blend_coeff(label: np.ndarray) -> np.ndarray:
     h, w = a.shape
     out = np.empty((h, w), dtype=np.float64)
     lib().oracle_blend_coeff(a.ctypes.data_as(_U8), h, w, _d(out))
+    return out
+
+
+def blend_coeff_at(label: np.ndarray, ys, xs) -> np.ndarray:
+    """Eq. (1) at the pixels (ys[i], xs[i]) only (brute force per pixel)."""
+    a = np.ascontiguousarray(label, dtype=np.uint8)
+    h, w = a.shape
+    ys = np.ascontiguousarray(ys, dtype=np.int32)
+    xs = np.ascontiguousarray(xs, dtype=np.int32)
+    out = np.empty(ys.shape, dtype=np.float64)
+    ip = ctypes.POINTER(ctypes.c_int)
+    lib().oracle_blend_coeff_at(a.ctypes.data_as(_U8), h, w, ys.ctypes.data_as(ip), xs.ctypes.data_as(ip),
+                                ys.size, _d(out))
     return out
 
 

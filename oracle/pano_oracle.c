@@ -438,6 +438,45 @@ void oracle_blend_coeff(const unsigned char* label, int h, int w, double* blend)
         }
 }
 
+/* Eq. (1) at n chosen pixels (ys[i], xs[i]) of a labelled canvas, by the same
+   brute force: for checks of large canvases at sampled pixels. */
+void oracle_blend_coeff_at(const unsigned char* label, int h, int w, const int* ys, const int* xs, long n,
+                           double* out)
+{
+    int has1 = 0, has2 = 0;
+    for (long k = 0; k < (long)h * w; ++k) {
+        has1 |= label[k] == 1;
+        has2 |= label[k] == 2;
+    }
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long k = 0; k < n; ++k) {
+        int i = ys[k], j = xs[k];
+        unsigned char a = PIX(label, w, i, j);
+        double v;
+        if (a == 1) v = 0.0;
+        else if (a == 2) v = 1.0;
+        else if (a == 3) {
+            if (!has1 && !has2) v = 0.5;
+            else if (!has1) v = 1.0;
+            else if (!has2) v = 0.0;
+            else {
+                double l2 = INFINITY, r2 = INFINITY;
+                for (int y = 0; y < h; ++y)
+                    for (int x = 0; x < w; ++x) {
+                        unsigned char b = PIX(label, w, y, x);
+                        if (b != 1 && b != 2) continue;
+                        double d2 = (double)(y - i) * (y - i) + (double)(x - j) * (x - j);
+                        if (b == 1 && d2 < l2) l2 = d2;
+                        if (b == 2 && d2 < r2) r2 = d2;
+                    }
+                double lmin = sqrt(l2), rmin = sqrt(r2);
+                v = lmin / (lmin + rmin);
+            }
+        } else v = 0.5;
+        out[k] = v;
+    }
+}
+
 /* ---------------------------------------------------------------------------
  * Eq. (1) for an overlap strip of width w that spans the canvas height, with
  * Area1 the column just left of it and Area2 the column just right of it:

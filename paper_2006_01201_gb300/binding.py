@@ -87,6 +87,8 @@ SIGNATURES = {
     "pano_stage_pyr_down": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
     "pano_stage_lk": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _VP], _I),
     "pano_stage_warp": ([_IMG, _VP, _F, _IMG, _VP], _I),
+    "pano_blend_coeff_scratch_bytes": ([_I, _I], ctypes.c_size_t),
+    "pano_blend_coeff": ([_VP, _I, _I, ctypes.c_size_t, _VP, _I, _VP, ctypes.c_size_t, _VP], _I),
     "pano_rig_create": ([_PAR, ctypes.POINTER(PanoRigDesc), _PP], _I),
     "pano_rig_run": ([_VP, _IMG, _IMG, _PP, _PP, _IMG, _I, _VP], _I),
     "pano_rig_autotune": ([_VP, _IMG, _IMG, _I, _VP], _I),
@@ -461,6 +463,33 @@ class Rig:
     @property
     def graph_captures(self) -> int:
         return int(load_library().pano_rig_graph_captures(self._h))
+
+
+AREA1, AREA2, AREA3 = 1, 2, 3   # labels of pano_blend_coeff
+
+
+def blend_coeff(label, out=None, scratch=None, stream=None):
+    """Eq. (1) on a labelled canvas: label is a uint8 CUDA tensor (H, W) with
+    1 = Area1, 2 = Area2, 3 = Area3 (overlap), other = neither; returns the
+    float32 (H, W) Blend array. scratch: optional uint8 device tensor of
+    pano_blend_coeff_scratch_bytes(H, W) bytes, reused across calls."""
+    torch = _torch()
+    if label.dtype != torch.uint8 or label.dim() != 2 or not label.is_cuda or label.stride(1) != 1:
+        raise PanoError(PANO_ERR_INVALID_ARG, "label must be a uint8 (H, W) CUDA tensor with contiguous rows")
+    h, w = label.shape
+    lib = load_library()
+    need = int(lib.pano_blend_coeff_scratch_bytes(h, w))
+    if out is None:
+        out = torch.empty((h, w), dtype=torch.float32, device=label.device)
+    if scratch is None:
+        scratch = torch.empty(need, dtype=torch.uint8, device=label.device)
+    if out.dtype != torch.float32 or out.dim() != 2 or out.stride(1) != 1 or tuple(out.shape) != (h, w):
+        raise PanoError(PANO_ERR_INVALID_ARG, "out must be a float32 (H, W) tensor with contiguous rows")
+    lp = label.stride(0) if h > 1 else w
+    bp = out.stride(0) if h > 1 else w
+    _check(lib.pano_blend_coeff(label.data_ptr(), h, w, lp, out.data_ptr(), bp, scratch.data_ptr(),
+                                scratch.numel() * scratch.element_size(), _stream_ptr(stream)))
+    return out
 
 
 class _DeviceArray:

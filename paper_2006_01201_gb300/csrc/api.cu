@@ -128,6 +128,7 @@ pano_status ensure_lk_ready(int* max_smem_out) {
     if (ms <= 0) return fail(PANO_ERR_CUDA, "cannot query the shared-memory limit");
     if (dev >= 0 && dev < 64 && !prepared[dev]) {
         if ((e = lk_prepare(ms)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        if ((e = blend_coeff_prepare(ms)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         prepared[dev] = 1;
     }
     *max_smem_out = ms;

@@ -215,6 +215,13 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
 cudaError_t launch_rig_blend(const RigBlendArgs& r, cudaStream_t s);
 cudaError_t launch_warp(const WarpArgs& a, cudaStream_t s);
 
+// Eq. (1) on a labelled canvas through an exact distance transform (edt.cu).
+size_t blend_coeff_scratch_bytes(int h, int w);
+size_t blend_coeff_row_smem(int w);
+cudaError_t blend_coeff_prepare(int max_smem_bytes);
+cudaError_t launch_blend_coeff(const unsigned char* label, int h, int w, long long pitch, float* blend,
+                               int blend_pitch, void* scratch, cudaStream_t s);
+
 cudaError_t launch_energy_grad(const EnergyArgs& a, cudaStream_t s);
 cudaError_t launch_pyr_down_adjoint(const float* gdst, int h, int w, int dst_pitch, float* gsrc, int src_pitch,
                                     cudaStream_t s);

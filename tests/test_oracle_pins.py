@@ -323,6 +323,20 @@ def test_blend_coeff_matches_scipy_edt_on_random_masks():
     np.testing.assert_allclose(oracle.blend_coeff(label), expect, rtol=0, atol=1e-14)
 
 
+def test_blend_coeff_at_sampled_pixels_matches_scipy_edt():
+    g = rng(16)
+    label = g.choice([0, 1, 2, 3], p=[0.05, 0.02, 0.03, 0.9], size=(40, 70)).astype(np.uint8)
+    dl = ndimage.distance_transform_edt(label != 1)
+    dr = ndimage.distance_transform_edt(label != 2)
+    expect = np.where(label == 1, 0.0, np.where(label == 2, 1.0, np.where(label == 3, dl / (dl + dr), 0.5)))
+    ys, xs = np.nonzero(np.ones_like(label))
+    got = oracle.blend_coeff_at(label, ys, xs).reshape(label.shape)
+    np.testing.assert_allclose(got, expect, rtol=0, atol=1e-14)
+    lab = np.full((4, 6), 3, np.uint8)
+    lab[0, 0] = 2
+    assert (oracle.blend_coeff_at(lab, [1, 3], [2, 5]) == 1.0).all()
+
+
 def test_blend_coeff_with_a_missing_area_is_the_limit_of_eq1():
     # no Area1 pixel: Lmin -> infinity, Lmin / (Lmin + Rmin) -> 1; no Area2: -> 0
     lab = np.full((3, 5), 3, np.uint8)
