@@ -121,13 +121,15 @@ __global__ void __launch_bounds__(kRowThreads) edt_rows_blend_kernel(const unsig
                                                                      const int* __restrict__ gL,
                                                                      const int* __restrict__ gR,
                                                                      float* __restrict__ blend, int blend_pitch) {
-    extern __shared__ int s_sites[];
-    __shared__ int s_k[2];
+    // dynamic shared memory only (the kernel's limit is set to the device
+    // maximum): the two envelope sizes, then the sites of each envelope
+    extern __shared__ int s_dyn[];
+    int* s_k = s_dyn;
+    int* vL = s_dyn + 2;
+    int* vR = vL + w;
     const int y = blockIdx.x;
     const int* rowL = gL + (long long)y * w;
     const int* rowR = gR + (long long)y * w;
-    int* vL = s_sites;
-    int* vR = s_sites + w;
     if (threadIdx.x == 0) s_k[0] = build_envelope(rowL, w, vL);
     if (threadIdx.x == 32) s_k[1] = build_envelope(rowR, w, vR);
     __syncthreads();
@@ -161,7 +163,7 @@ __global__ void __launch_bounds__(kRowThreads) edt_rows_blend_kernel(const unsig
 
 size_t blend_coeff_scratch_bytes(int h, int w) { return (size_t)2 * h * w * sizeof(int); }
 
-size_t blend_coeff_row_smem(int w) { return (size_t)2 * w * sizeof(int); }
+size_t blend_coeff_row_smem(int w) { return (size_t)(2 * w + 2) * sizeof(int); }
 
 cudaError_t blend_coeff_prepare(int max_smem_bytes) {
     return cudaFuncSetAttribute(edt_rows_blend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
