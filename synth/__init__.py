@@ -205,14 +205,14 @@ def _parallax_field(rng: np.random.Generator, h: int, w: int, dmax: float):
 
 
 def pair_fullres_rgb(seed: int = 1, h: int = 4000, w: int = 1500, dmax: float = 20.0,
-                     levels: int = 6) -> Pair:
+                     levels: int = 6, gain_range: Optional[tuple] = (0.9, 1.1)) -> Pair:
     """4000x1500 RGB uint8 pair: colour texture, 0-dmax px parallax with steps,
-    per-channel gain U(0.9, 1.1) and N(0, 2/255) noise."""
+    per-channel gain U(gain_range) (None: no gain) and N(0, 2/255) noise."""
     rng = np.random.default_rng(10_000 + seed)
     dfun = _parallax_field(rng, h, w, dmax)
     return make_pair(f"pair_{h}x{w}_rgb_u8", h, w, 3, "u8", seed, dfun, levels,
-                     noise_std=2.0 / 255.0, gain_range=(0.9, 1.1),
-                     meta={"field": "parallax", "dmax": dmax})
+                     noise_std=2.0 / 255.0, gain_range=gain_range,
+                     meta={"field": "parallax", "dmax": dmax, "gain_range": gain_range})
 
 
 def pair_translation(dx: float, dy: float, seed: int = 5, h: int = 96, w: int = 128,
