@@ -40,7 +40,7 @@ STREAM_MIN_PIXELS = 100000   # levels with at least this many pixels use the str
 # DRAM bytes (read + write) per launch of the dominant kernel, averaged over
 # its launches in one step, from an ncu capture of the current kernel; None
 # when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (171.124e6 + 4.653e6 + 18.478e6) / 3}
+TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (171.411968e6 + 4.652544e6 + 18.478336e6) / 3}
 
 
 # ---------------------------------------------------------------------------
