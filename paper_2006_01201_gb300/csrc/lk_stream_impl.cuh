@@ -85,6 +85,12 @@ struct StreamGeom {
 
 __device__ __forceinline__ int ring_slot(int y) { return (y + kRingOff) & (kRing - 1); }
 
+// Paired FP32 arithmetic (one instruction for the two lanes of a float2;
+// each lane rounds exactly as the scalar operation would).
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
 __device__ __forceinline__ void copy_async4(void* dst_smem, const void* src) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst_smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
@@ -124,7 +130,8 @@ struct TargetBox {
 // taps lie in it, else from global memory. Both paths read the same values.
 template <int JW, class Ts>
 __device__ __forceinline__ float sample_target(const TargetBox<Ts>& b, int x, int y, int rx, float2 ref, float2 u) {
-    const float ox = ref.x + u.x, oy = ref.y + u.y;
+    const float2 o = add2(ref, u);
+    const float ox = o.x, oy = o.y;
     const float fx = floorf(ox), fy = floorf(oy);
     const int ix = (int)fx, iy = (int)fy;
     const int bcol = rx + (ix - b.fref_x) + kMX;
@@ -146,32 +153,35 @@ __device__ __forceinline__ float2 residual_product(const TargetBox<Ts>& b, int x
                                                    float2 u, float2 g, float t) {
     const float Jw = sample_target<JW, Ts>(b, x, y, rx, ref, u);
     const float s = fmaf(g.x, u.x, fmaf(g.y, u.y, t - Jw));
-    return make_float2(g.x * s, g.y * s);
+    return mul2(g, make_float2(s, s));
 }
 
-// Column sums over 2R+1 rows of the product buffer for one column: the
-// CH + 2R values are read once into registers and every output row is summed
-// directly from them (no running sums, which would carry rounding from one
-// row into the next). Also saves the last 2R product rows as the history of
-// this stage for the next chunk.
-template <int RAD, int CH, int RW>
+// Column sums over 2R+1 rows of the product buffer for the output rows
+// [part * CH / S, (part + 1) * CH / S) of one column: the CH / S + 2R values
+// are read once into registers and every output row is summed directly from
+// them (no running sums, which would carry rounding from one row into the
+// next). The part with the last rows also saves the last 2R product rows as
+// the history of this stage for the next chunk.
+template <int RAD, int CH, int RW, int S>
 __device__ __forceinline__ void column_sums(const float2* __restrict__ sP, float2* __restrict__ sV,
-                                            float2* __restrict__ hist, int rx) {
-    float2 p[CH + 2 * RAD];
+                                            float2* __restrict__ hist, int rx, int part) {
+    static_assert(CH % S == 0, "parts must split the chunk rows evenly");
+    constexpr int HC = CH / S;
+    const int r0 = part * HC;
+    float2 p[HC + 2 * RAD];
 #pragma unroll
-    for (int d = 0; d < CH + 2 * RAD; ++d) p[d] = sP[d * RW + rx];
+    for (int d = 0; d < HC + 2 * RAD; ++d) p[d] = sP[(r0 + d) * RW + rx];
 #pragma unroll
-    for (int yy = 0; yy < CH; ++yy) {
+    for (int yy = 0; yy < HC; ++yy) {
         float2 v = p[yy];
 #pragma unroll
-        for (int d = 1; d <= 2 * RAD; ++d) {
-            v.x += p[yy + d].x;
-            v.y += p[yy + d].y;
-        }
-        sV[yy * RW + rx] = v;
+        for (int d = 1; d <= 2 * RAD; ++d) v = add2(v, p[yy + d]);
+        sV[(r0 + yy) * RW + rx] = v;
     }
+    if (part == S - 1) {
 #pragma unroll
-    for (int d = 0; d < 2 * RAD; ++d) hist[d * RW + rx] = p[CH + d];
+        for (int d = 0; d < 2 * RAD; ++d) hist[d * RW + rx] = p[HC + d];
+    }
 }
 
 // One work item: direction `dir`, band `bx` (BW output columns) and segment
@@ -190,7 +200,7 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
     constexpr int kJPT = (Geo::JW + TX - 1) / TX;  // target-row elements per thread (16-bit planes)
     float jnext[kJPT];
     (void)jnext;
-    static_assert(RW <= kCsT0 && kCsT0 + 2 * RW <= kStreamThreads && CH % 2 == 0, "B_1 thread groups");
+    static_assert(2 * RW <= kCsT0 && kCsT0 + 2 * RW <= kStreamThreads && CH % 2 == 0, "B_1 thread groups");
     float* sT = reinterpret_cast<float*>(smem + Geo::kT);
     float2* sG = reinterpret_cast<float2*>(smem + Geo::kG);
     float2* sU = reinterpret_cast<float2*>(smem + Geo::kU);
@@ -238,8 +248,9 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
     // [a0n, a0n + CH) reads from global memory: template rows a0n-1 .. a0n+CH
     // (columns ox-1 .. ox+RW, clamp-to-edge) and, when the level starts from
     // the coarser level, the coarse flow rows and columns its upsampling taps.
-    auto stage_inputs = [&](int a0n) {
-        for (int i = tid; i < TSH * TSW; i += kStreamThreads) {
+    // Staged by nw workers, this thread being worker wi.
+    auto stage_inputs = [&](int a0n, int wi, int nw) {
+        for (int i = wi; i < TSH * TSW; i += nw) {
             const int r = i / TSW, cc = i - r * TSW;
             const int ys = min(max(a0n - 1 + r, 0), h - 1), xs = min(max(ox - 1 + cc, 0), w - 1);
             if constexpr (kAsyncT) copy_async4(sTS + i, T + (long long)ys * pitchT + xs);
@@ -247,7 +258,7 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
         }
         if (stage_flow) {
             const int cy0 = a0n >> 1, cx0 = ox >> 1;
-            for (int i = tid; i < FSH * FSW; i += kStreamThreads) {
+            for (int i = wi; i < FSH * FSW; i += nw) {
                 const int r = i / FSW, cc = i - r * FSW;
                 const int ys = min(max(cy0 + r, 0), a.in_h - 1), xs = min(max(cx0 + cc, 0), a.in_w - 1);
                 copy_async8(sFS + i, ucoarse + (long long)ys * D.uin_pitch + xs);
@@ -258,7 +269,7 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
 
     const int c_first = -((2 * K * RAD + CH - 1) / CH);
     const int c_last = (Y1 - Y0 + CH - 1) / CH - 1;
-    stage_inputs(Y0 + K * RAD + c_first * CH);
+    stage_inputs(Y0 + K * RAD + c_first * CH, tid, kStreamThreads);
     // Rings start at zero: the column sums of the first chunk read ring rows
     // that no earlier chunk wrote (their results are discarded, but must
     // stay finite).
@@ -328,13 +339,16 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
             }
         }
         __syncthreads();
-        // the staging buffers are free again: start fetching the next chunk's inputs
-        if (c < c_last) stage_inputs(a0 + CH);
-        // ---- B_1: column sums of stage 1 (one thread per column, the column's
-        //      values read once into registers) and its history; column sums
-        //      of grad T grad T^T for the normal matrices of rows [a1, a1 + CH)
-        if (tid < RW) {
-            column_sums<RAD, CH, RW>(sP, sV, sH, tid);
+        // the staging buffers are free again: every thread starts fetching
+        // part of the next chunk's inputs
+        if (c < c_last) stage_inputs(a0 + CH, tid, kStreamThreads);
+        // ---- B_1: column sums of stage 1 (two threads per column, the
+        //      column's values read once into registers) and its history;
+        //      column sums of grad T grad T^T for the normal matrices of rows
+        //      [a1, a1 + CH)
+        if (tid < 2 * RW) {
+            const int part = tid >= RW;
+            column_sums<RAD, CH, RW, 2>(sP, sV, sH, tid - part * RW, part);
         } else if (tid >= kCsT0 && tid < kCsT0 + 2 * RW) {
             // normal-matrix column sums: two threads per column, CH/2 rows each
             const int rx = (tid - kCsT0) % RW, half = (tid - kCsT0) / RW;
@@ -345,15 +359,15 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
             for (int d = 0; d < HC + 2 * RAD; ++d) g[d] = sG[ring_slot(yb + d) * RW + rx];
 #pragma unroll
             for (int yy = 0; yy < HC; ++yy) {
-                float c11 = 0.f, c12 = 0.f, c22 = 0.f;
+                float2 c1 = make_float2(0.f, 0.f);  // (c11, c12)
+                float c22 = 0.f;
 #pragma unroll
                 for (int d = 0; d <= 2 * RAD; ++d) {
-                    c11 = fmaf(g[yy + d].x, g[yy + d].x, c11);
-                    c12 = fmaf(g[yy + d].x, g[yy + d].y, c12);
+                    c1 = fma2(make_float2(g[yy + d].x, g[yy + d].x), g[yy + d], c1);
                     c22 = fmaf(g[yy + d].y, g[yy + d].y, c22);
                 }
                 const int o = (half * HC + yy) * RW + rx;
-                sCSA[o] = make_float2(c11, c12);
+                sCSA[o] = c1;
                 sCSB[o] = c22;
             }
         }
@@ -413,26 +427,24 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                     float2 m0 = vv[HR - RAD], m1 = vv[HR - RAD + 1];
 #pragma unroll
                     for (int d = 1; d <= 2 * RAD; ++d) {
-                        m0.x += vv[HR - RAD + d].x;
-                        m0.y += vv[HR - RAD + d].y;
-                        m1.x += vv[HR - RAD + d + 1].x;
-                        m1.y += vv[HR - RAD + d + 1].y;
+                        m0 = add2(m0, vv[HR - RAD + d]);
+                        m1 = add2(m1, vv[HR - RAD + d + 1]);
                     }
                     float2 ga0, ga1;
                     float gb0, gb1;
                     if (k == 1) {
                         const float2* ca = sCSA + ty * RW + xp;
                         const float* cb = sCSB + ty * RW + xp;
-                        float a11 = 0.f, a12 = 0.f, a22 = 0.f, b11 = 0.f, b12 = 0.f, b22 = 0.f;
+                        float2 a1 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);  // (x11, x12)
+                        float a22 = 0.f, b22 = 0.f;
 #pragma unroll
                         for (int d = -RAD; d <= RAD; ++d) {
-                            a11 += ca[d].x;
-                            a12 += ca[d].y;
+                            a1 = add2(a1, ca[d]);
                             a22 += cb[d];
-                            b11 += ca[d + 1].x;
-                            b12 += ca[d + 1].y;
+                            b1 = add2(b1, ca[d + 1]);
                             b22 += cb[d + 1];
                         }
+                        const float a11 = a1.x, a12 = a1.y, b11 = b1.x, b12 = b1.y;
                         const float p11 = a11 + lam, p22 = a22 + lam;
                         const float ip = 1.0f / (p11 * p22 - a12 * a12);
                         const float q11 = b11 + lam, q22 = b22 + lam;
@@ -453,22 +465,23 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                     }
                     const float4 u4 = *reinterpret_cast<const float4*>(sU + srow + xp);
                     float2 v0 = make_float2(u4.x, u4.y), v1 = make_float2(u4.z, u4.w);
+                    const float2 lam2 = make_float2(lam, lam);
                     if (in0) {
-                        const float r1 = fmaf(lam, v0.x, m0.x), r2 = fmaf(lam, v0.y, m0.y);
-                        v0 = make_float2(fmaf(ga0.x, r1, ga0.y * r2), fmaf(ga0.y, r1, gb0 * r2));
+                        const float2 r = fma2(lam2, v0, m0);
+                        v0 = fma2(ga0, make_float2(r.x, r.x), mul2(make_float2(ga0.y, gb0), make_float2(r.y, r.y)));
                     }
                     if (in1) {
-                        const float r1 = fmaf(lam, v1.x, m1.x), r2 = fmaf(lam, v1.y, m1.y);
-                        v1 = make_float2(fmaf(ga1.x, r1, ga1.y * r2), fmaf(ga1.y, r1, gb1 * r2));
+                        const float2 r = fma2(lam2, v1, m1);
+                        v1 = fma2(ga1, make_float2(r.x, r.x), mul2(make_float2(ga1.y, gb1), make_float2(r.y, r.y)));
                     }
                     *reinterpret_cast<float4*>(sU + srow + xp) = make_float4(v0.x, v0.y, v1.x, v1.y);
                     if (k == K) {
                         if (row_in && y >= Y0 && y < Y1) {
                             float2* uo = reinterpret_cast<float2*>(D.uout) + (long long)y * D.uout_pitch;
                             if (in0 && xp >= K * RAD && xp < K * RAD + BW)
-                                uo[ox + xp] = make_float2(v0.x + ref.x, v0.y + ref.y);
+                                uo[ox + xp] = add2(v0, ref);
                             if (in1 && xp + 1 >= K * RAD && xp + 1 < K * RAD + BW)
-                                uo[ox + xp + 1] = make_float2(v1.x + ref.x, v1.y + ref.y);
+                                uo[ox + xp + 1] = add2(v1, ref);
                         }
                     } else {
                         // products of stage k+1 at the same two pixels
@@ -498,9 +511,13 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
             }
             __syncthreads();
             if (k < K) {
-                // ---- B_{k+1}: column sums of stage k+1 and its history
-                const int rx = c0 + tid;
-                if (rx < RW - c0) column_sums<RAD, CH, RW>(sP, sV, sH + (size_t)k * 2 * RAD * RW, rx);
+                // ---- B_{k+1}: column sums of stage k+1 and its history (two
+                //      threads per column)
+                const int ncol = RW - 2 * c0;
+                if (tid < 2 * ncol) {
+                    const int part = tid >= ncol;
+                    column_sums<RAD, CH, RW, 2>(sP, sV, sH + (size_t)k * 2 * RAD * RW, c0 + tid - part * ncol, part);
+                }
                 __syncthreads();
             }
         }
