@@ -36,7 +36,8 @@ UNIT = "MP/s"
 WORKLOAD = {"workload": "pair_4000x1500_rgb_u8_lv6", "h": 4000, "w": 1500, "channels": 3, "levels": 6,
             "iters": 5, "radius": 2}
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
-STREAM_MIN_PIXELS = 100000   # levels with at least this many pixels use the streamed LK kernel
+STREAM_MIN_PIXELS = 50000    # levels with at least this many pixels use the streamed LK kernel
+SMALL_TILE_PIXELS = 16000    # tiled levels below this many pixels use 16 x 8 tiles
 # DRAM bytes (read + write) per launch of the dominant kernel, averaged over
 # its launches in one step, from an ncu capture of the current kernel; None
 # when the kernel has changed since the counters were taken.
@@ -90,10 +91,12 @@ PANO_LK_AUTO, PANO_LK_STREAM, PANO_LK_TILE = 0, 1, 2
 PYR_DTYPES = {"f32": (1, 0, 4), "bf16": (2, 1, 2), "f16": (3, 2, 2)}
 
 
-def rig_level_kernels(h: int, widths, levels: int, kernels):
+def rig_level_kernels(h: int, widths, levels: int, kernels, tiles=None):
     """Kernel launches of each LK level of a rig, in launch order: for level
-    l, [(kernel name, [pairs])] with the streamed batch first. kernels[l] is
-    the level's PANO_LK_* tuning; AUTO uses the single-pair size rule."""
+    l, [(kernel name, [pairs])], the streamed batch first, then one tiled
+    launch per tile shape (in the order of the first pair with it).
+    kernels[l] is the level's PANO_LK_* tuning and tiles[l] its (tile_w,
+    tile_h), (0, 0) for the default; AUTO uses the single-pair rules."""
     out = []
     for l in range(levels):
         hl = h
@@ -101,15 +104,20 @@ def rig_level_kernels(h: int, widths, levels: int, kernels):
         for _ in range(l):
             hl = (hl + 1) // 2
             ws = [(w + 1) // 2 for w in ws]
-        st, ti = [], []
+        tile = tuple(tiles[l]) if tiles else (0, 0)
+        st, groups = [], {}
         for k, w in enumerate(ws):
             use = kernels[l] == PANO_LK_STREAM or (kernels[l] == PANO_LK_AUTO and hl * w >= STREAM_MIN_PIXELS)
-            (st if use else ti).append(k)
+            if use:
+                st.append(k)
+                continue
+            shape = tile if tile != (0, 0) else ("small" if hl * w < SMALL_TILE_PIXELS else "default")
+            groups.setdefault(shape, []).append(k)
         lev = []
         if st:
             lev.append(("lk_stream_batch_kernel", st))
-        if ti:
-            lev.append(("lk_level_batch_kernel", ti))
+        for members in groups.values():
+            lev.append(("lk_level_batch_kernel", members))
         out.append(lev)
     return out
 
@@ -648,7 +656,8 @@ def run_rig(args):
     torch.cuda.synchronize()
     recs = rig.trace_read(64 * args.steps)
     rig.trace_enable(0, 0)
-    plan = rig_level_kernels(h, widths, levels, [t["kernel"] for t in tunings])
+    plan = rig_level_kernels(h, widths, levels, [t["kernel"] for t in tunings],
+                             [(t["tile_w"], t["tile_h"]) for t in tunings])
     names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "rig_blend_kernel"}
     per_kind, lk_seen = {}, {}
     stream_bytes = 0.0

@@ -10,10 +10,10 @@
  *
  *   luma of all strips          one launch
  *   REDUCE of all strips        one launch per level
- *   LK, both directions, every  one launch per level and kernel kind: a
- *   pair                        persistent launch of the streamed kernel
- *                               over the (pair, direction, band, segment)
- *                               work list, or one tiled grid over all pairs
+ *   LK, both directions, every  per level, one persistent launch of the
+ *   pair                        streamed kernel over the (pair, direction,
+ *                               band, segment) work list and/or one tiled
+ *                               grid per tile shape over those pairs
  *   blend into the canvas       one launch
  *
  * The whole sequence can be captured once in a CUDA graph and replayed. The
@@ -63,7 +63,8 @@ typedef struct pano_rig_desc {
 
 /* Kernel of one LK level. */
 #define PANO_LK_AUTO   0  /* per pair, as pano_flow_pair: streamed for levels of at least
-                             100000 pixels (1 <= iters <= 5), tiled below */
+                             50000 pixels (1 <= iters <= 5), tiled below (16 x 8 tiles
+                             below 16000 pixels) */
 #define PANO_LK_STREAM 1  /* streamed kernel for every pair (needs 1 <= iters <= 5) */
 #define PANO_LK_TILE   2  /* tiled kernel for every pair */
 

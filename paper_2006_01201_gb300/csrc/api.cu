@@ -316,8 +316,7 @@ void pair_lk_args(const pano_flow_ctx* c, const PairPlanes& pp, int l, float* fl
     ka->iters = c->p.iters;
     ka->radius = c->p.radius;
     ka->lambda = c->p.lambda;
-    ka->tile_w = c->tile_w;
-    ka->tile_h = c->tile_h;
+    lk_level_tile(ka->w, ka->h, c->tile_w, c->tile_h, &ka->tile_w, &ka->tile_h);
     ka->pyr = pyr_type(c->p.pyr_dtype);
 }
 

@@ -200,7 +200,20 @@ cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s);
 cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s);
 // One LK level: streamed (lk_stream.cu) for levels of at least
 // kStreamMinPixels pixels and 1 <= iters <= 5, tiled (lk.cu) otherwise.
-constexpr long long kStreamMinPixels = 100000;
+// Levels below kSmallTilePixels use small tiles (kSmallTileW x kSmallTileH):
+// their few large tiles would leave most SMs idle, and the time of such a
+// level is the latency of one tile. (Measured on GB300: a 94k-pixel level
+// takes 38 us streamed and 51 us tiled; a 5.9k-pixel level 15 us on 16x8
+// tiles and 21 us on 32x16.)
+constexpr long long kStreamMinPixels = 50000;
+constexpr long long kSmallTilePixels = 16000;
+constexpr int kSmallTileW = 16, kSmallTileH = 8;
+// Tile of the tiled kernel for a level of w x h pixels, given the default.
+inline void lk_level_tile(int w, int h, int def_w, int def_h, int* tw, int* th) {
+    const bool small = (long long)w * h < kSmallTilePixels;
+    *tw = small ? kSmallTileW : def_w;
+    *th = small ? kSmallTileH : def_h;
+}
 cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s);
 cudaError_t launch_lk_tile(const LkArgs& a, int ndirs, cudaStream_t s);
 cudaError_t launch_lk_tile_batch(const LkBatch& b, cudaStream_t s);

@@ -191,8 +191,12 @@ LkArgs pair_level_args(const pano_rig* r, const RunCall& c, int k, int l, const 
     a.iters = r->p.iters;
     a.radius = r->p.radius;
     a.lambda = r->p.lambda;
-    a.tile_w = t.tile_w ? t.tile_w : r->def_tile_w;
-    a.tile_h = t.tile_h ? t.tile_h : r->def_tile_h;
+    if (t.tile_w) {
+        a.tile_w = t.tile_w;
+        a.tile_h = t.tile_h;
+    } else {
+        lk_level_tile(a.w, a.h, r->def_tile_w, r->def_tile_h, &a.tile_w, &a.tile_h);  // the rule of pano_flow_pair
+    }
     a.seg_rows = t.seg_rows;
     a.pyr = pyr_type(r->p.pyr_dtype);
     return a;
@@ -205,17 +209,29 @@ bool uses_stream(const pano_rig* r, const LkArgs& a, int kernel) {
     return (long long)a.w * a.h >= kStreamMinPixels;  // the rule of launch_lk_level
 }
 
-// LK level l of every pair with tuning t; returns the first launch error and
-// adds the kernels launched to *kernels.
+// LK level l of every pair with tuning t: one persistent launch of the
+// streamed kernel for the pairs that use it, then one tiled launch per tile
+// shape (in the order of the first pair with that shape). Returns the first
+// launch error and adds the kernels launched to *kernels.
 cudaError_t enqueue_lk_level(pano_rig* r, const RunCall& c, int l, const pano_rig_tuning& t, cudaStream_t s,
                              bool trace, int* kernels) {
-    LkBatch sb, tb;
+    LkBatch sb;
     memset(&sb, 0, sizeof(sb));
-    memset(&tb, 0, sizeof(tb));
+    LkBatch tb[kMaxBatch];
+    int ntb = 0;
     for (int k = 0; k < r->d.n_pairs; ++k) {
         LkArgs a = pair_level_args(r, c, k, l, t);
-        if (uses_stream(r, a, t.kernel)) sb.pair[sb.n++] = a;
-        else tb.pair[tb.n++] = a;
+        if (uses_stream(r, a, t.kernel)) {
+            sb.pair[sb.n++] = a;
+            continue;
+        }
+        int g = 0;
+        while (g < ntb && (tb[g].pair[0].tile_w != a.tile_w || tb[g].pair[0].tile_h != a.tile_h)) ++g;
+        if (g == ntb) {
+            memset(&tb[g], 0, sizeof(tb[g]));
+            ++ntb;
+        }
+        tb[g].pair[tb[g].n++] = a;
     }
     cudaError_t e;
     if (sb.n) {
@@ -225,9 +241,9 @@ cudaError_t enqueue_lk_level(pano_rig* r, const RunCall& c, int l, const pano_ri
         if (slot >= 0) trace_end(r->tr, slot, s);
         ++*kernels;
     }
-    if (tb.n) {
+    for (int g = 0; g < ntb; ++g) {
         int slot = trace ? trace_begin(r->tr, PANO_TRACE_LK, l, s) : -1;
-        if ((e = launch_lk_tile_batch(tb, s)) != cudaSuccess) return e;
+        if ((e = launch_lk_tile_batch(tb[g], s)) != cudaSuccess) return e;
         if (slot >= 0) trace_end(r->tr, slot, s);
         ++*kernels;
     }

@@ -74,10 +74,15 @@ def test_warmup_below_three_is_rejected():
 def test_rig_level_kernels_follow_the_size_rule_and_forced_kinds():
     widths = bench.RIG_WORKLOAD["widths"]
     plan = bench.rig_level_kernels(4000, widths, 6, [bench.PANO_LK_AUTO] * 6)
-    # level 3 is 500 rows: widths >= 200 give >= 100000 pixels
-    assert plan[3] == [("lk_stream_batch_kernel", [5, 6, 7]), ("lk_level_batch_kernel", [0, 1, 2, 3, 4])]
+    # level 3 is 500 rows: every width (>= 100) gives >= 50000 pixels; level 4
+    # (250 rows) is tiled, with 16 x 8 tiles for the pairs below 16000 pixels
+    # (widths 50 and 60); level 5 is small for every pair
+    assert plan[3] == [("lk_stream_batch_kernel", list(range(8)))]
+    assert plan[4] == [("lk_level_batch_kernel", [0, 1]), ("lk_level_batch_kernel", [2, 3, 4, 5, 6, 7])]
     assert plan[0] == [("lk_stream_batch_kernel", list(range(8)))]
     assert plan[5] == [("lk_level_batch_kernel", list(range(8)))]
+    tuned = bench.rig_level_kernels(4000, widths, 6, [bench.PANO_LK_TILE] * 6, [(32, 8)] * 6)
+    assert all(p == [("lk_level_batch_kernel", list(range(8)))] for p in tuned)
     forced = bench.rig_level_kernels(4000, widths, 6, [bench.PANO_LK_TILE] + [bench.PANO_LK_STREAM] * 5)
     assert forced[0] == [("lk_level_batch_kernel", list(range(8)))]
     assert all(p == [("lk_stream_batch_kernel", list(range(8)))] for p in forced[1:])

@@ -43,11 +43,13 @@ def epe(a, b):
     return np.hypot(*(a - b).transpose(2, 0, 1))
 
 
-# h = 400: level 0 of the 240-wide pair has 96000 pixels (tiled kernel), of
-# the 300-wide pair 120000 (streamed kernel), so level 0 is split over both
-# kernel kinds; the third span wraps around the canvas seam and covers the
+# h = 400: level 0 of the 100-wide pair has 40000 pixels (tiled kernel), of
+# the others 96000 and 70400 (streamed kernel), so level 0 is split over both
+# kernel kinds; at level 1 the 100-wide pair drops below 16000 pixels and
+# gets the small tiles while the others keep the default ones (two tiled
+# launches). The third span wraps around the canvas seam and covers the
 # start of the first.
-GEOM = dict(h=400, widths=(240, 300, 176), x0=(0, 200, 520), canvas=(420, 600), y0=10, levels=4)
+GEOM = dict(h=400, widths=(240, 100, 176), x0=(0, 200, 520), canvas=(420, 600), y0=10, levels=4)
 
 
 @pytest.fixture(scope="module")
@@ -99,8 +101,8 @@ def test_default_tuning_equals_single_pair_path_and_places_canvas(small_rig_pair
         place(expect, [F.cpu().numpy() for _, _, F in ref])
         got = canvas.cpu().numpy()
         assert np.array_equal(got, expect)
-        # columns 500..519 lie in no span and rows outside the strips are untouched
-        assert (got[:, 500:520] == SENTINEL).all()
+        # columns 300..519 lie in no span and rows outside the strips are untouched
+        assert (got[:, 300:520] == SENTINEL).all()
         assert (got[:GEOM["y0"]] == SENTINEL).all() and (got[GEOM["y0"] + GEOM["h"]:] == SENTINEL).all()
 
 
