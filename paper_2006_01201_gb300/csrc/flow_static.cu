@@ -234,8 +234,7 @@ pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L
         ka.iters = p->iters;
         ka.radius = p->radius;
         ka.lambda = p->lambda;
-        ka.tile_w = tw;
-        ka.tile_h = th;
+        lk_level_tile(ka.w, ka.h, tw, th, &ka.tile_w, &ka.tile_h);  // as pano_flow_pair
         if ((e = launch_lk_level(ka, 2, s)) != cudaSuccess)
             return sfail(PANO_ERR_CUDA, "LK launch: %s", cudaGetErrorString(e));
     }
