@@ -97,10 +97,11 @@ PANO_API pano_status pano_rig_create(const pano_flow_params* p, const pano_rig_d
  *   canvas      canvas_h x canvas_w image with the rig's c and dtype, or
  *               NULL to compute flows only. It must not overlap any input.
  *   use_graph   0: enqueue the kernels directly. 1: replay a CUDA graph of
- *               the same sequence; the graph is captured on the first call
- *               and again whenever the call's pointers, pitches or the
- *               tuning differ from those of the last capture. Tracing
- *               records only calls with use_graph = 0.
+ *               the same sequence. The rig keeps up to 4 graphs, one per
+ *               distinct set of pointers, pitches and tuning (e.g. the two
+ *               buffer sets of a double-buffered pipeline); a call with a
+ *               new set captures a graph in place of the least recently
+ *               used one. Tracing records only calls with use_graph = 0.
  * The device that was current at pano_rig_create must be current.
  * Errors: INVALID_ARG, CUDA. */
 PANO_API pano_status pano_rig_run(pano_rig* rig, const pano_image* L, const pano_image* R,

@@ -284,6 +284,10 @@ class FlowContext:
             F_host.copy_(work["F"], non_blocking=True)
         return F_host
 
+    def host_pipeline(self, shape, dtype, device="cuda"):
+        """A HostPipeline of this context for strips of `shape` and `dtype`."""
+        return HostPipeline(self, shape, dtype, device)
+
     # -- tracing -------------------------------------------------------------
 
     def trace_enable(self, kind_mask: int, capacity: int) -> None:
@@ -301,6 +305,118 @@ class FlowContext:
     def launches(self) -> int:
         """Kernel launches enqueued by this context so far."""
         return int(load_library().pano_flow_launches(self._h))
+
+
+class _Pipeline:
+    """Two device buffer sets used in turn. Item k: the host->device copies of
+    its inputs run on the input stream once buffer set k % 2 is free again,
+    the kernels on the compute stream once its inputs have arrived, and the
+    device->host copy of its result on the output stream once they are done;
+    so the copies of items k + 1 and k - 1 overlap the kernels of item k.
+    Host buffers must be pinned, and each item's host output must stay
+    untouched until `wait(k)` (or `drain()`) returns."""
+
+    def __init__(self, bufs, compute_stream=None):
+        torch = _torch()
+        self.bufs = bufs
+        self.s_in = torch.cuda.Stream()
+        self.s_out = torch.cuda.Stream()
+        self.s_comp = compute_stream if compute_stream is not None else torch.cuda.Stream()
+        self.free = [None, None]          # event: buffer set b drained by the output stream
+        self.done = {}                    # item -> event recorded after its output copy
+
+    def _submit(self, k, upload, compute, download):
+        torch = _torch()
+        b = k % 2
+        buf = self.bufs[b]
+        if self.free[b] is not None:
+            self.s_in.wait_event(self.free[b])
+        with torch.cuda.stream(self.s_in):
+            upload(buf)
+            ev_in = torch.cuda.Event()
+            ev_in.record(self.s_in)
+        self.s_comp.wait_event(ev_in)
+        compute(buf, self.s_comp)
+        ev_c = torch.cuda.Event()
+        ev_c.record(self.s_comp)
+        self.s_out.wait_event(ev_c)
+        with torch.cuda.stream(self.s_out):
+            download(buf)
+            ev_out = torch.cuda.Event()
+            ev_out.record(self.s_out)
+        self.free[b] = ev_out
+        self.done[k] = ev_out
+        self.done.pop(k - 2, None)
+        return ev_out
+
+    def wait(self, k):
+        ev = self.done.get(k)
+        if ev is not None:
+            ev.synchronize()
+
+    def drain(self):
+        for ev in list(self.done.values()):
+            ev.synchronize()
+
+
+class HostPipeline(_Pipeline):
+    """Strip pairs from pinned host memory to blended strips in pinned host
+    memory through one FlowContext, with the copies of neighbouring pairs
+    overlapping the kernels of the current one (see _Pipeline)."""
+
+    def __init__(self, ctx: "FlowContext", shape, dtype, device="cuda", compute_stream=None):
+        torch = _torch()
+        h, w = shape[0], shape[1]
+        bufs = [{"L": torch.empty(shape, dtype=dtype, device=device), "R": torch.empty(shape, dtype=dtype, device=device),
+                 "lr": torch.empty((h, w, 2), dtype=torch.float32, device=device),
+                 "rl": torch.empty((h, w, 2), dtype=torch.float32, device=device),
+                 "F": torch.empty(shape, dtype=dtype, device=device)} for _ in range(2)]
+        super().__init__(bufs, compute_stream)
+        self.ctx = ctx
+
+    def submit(self, k: int, L_host, R_host, F_host):
+        """Enqueue pair k; returns the event that completes with its F_host."""
+        def upload(buf):
+            buf["L"].copy_(L_host, non_blocking=True)
+            buf["R"].copy_(R_host, non_blocking=True)
+
+        def compute(buf, s):
+            self.ctx.flow_pair(buf["L"], buf["R"], out=(buf["lr"], buf["rl"]), stream=s)
+            self.ctx.blend_pair(buf["L"], buf["R"], buf["lr"], buf["rl"], out=buf["F"], stream=s)
+
+        def download(buf):
+            F_host.copy_(buf["F"], non_blocking=True)
+
+        return self._submit(k, upload, compute, download)
+
+
+class RigHostPipeline(_Pipeline):
+    """Every pair of a rig from pinned host strips to a pinned host canvas,
+    overlapped as HostPipeline does (graph replays on the compute stream)."""
+
+    def __init__(self, rig: "Rig", device="cuda", compute_stream=None):
+        torch = _torch()
+        shapes = [(rig.h, w, rig.c) if rig.c > 1 else (rig.h, w) for w in rig.widths]
+        bufs = [{"L": [torch.empty(sh, dtype=rig.dtype, device=device) for sh in shapes],
+                 "R": [torch.empty(sh, dtype=rig.dtype, device=device) for sh in shapes],
+                 "canvas": rig.new_canvas(device)} for _ in range(2)]
+        super().__init__(bufs, compute_stream)
+        self.rig = rig
+
+    def submit(self, k: int, L_hosts, R_hosts, canvas_host, use_graph: bool = True):
+        def upload(buf):
+            for d, h_ in zip(buf["L"], L_hosts):
+                d.copy_(h_, non_blocking=True)
+            for d, h_ in zip(buf["R"], R_hosts):
+                d.copy_(h_, non_blocking=True)
+
+        def compute(buf, s):
+            self.rig.run(buf["L"], buf["R"], canvas=buf["canvas"], use_graph=use_graph, stream=s)
+
+        def download(buf):
+            canvas_host.copy_(buf["canvas"], non_blocking=True)
+
+        return self._submit(k, upload, compute, download)
 
 
 def flow_pair_static(params: Params, L, R, out=None, stream=None):

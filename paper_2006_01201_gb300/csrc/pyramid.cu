@@ -84,18 +84,43 @@ __global__ void __launch_bounds__(256) luma_kernel(const __grid_constant__ LumaA
 }
 
 // ---------------------------------------------------------------------------
-// REDUCE: a 32 x 8 tile of the destination per 256-thread block. The source
-// footprint (2*8+3 rows x 2*32+3 columns, clamped) is staged in shared
-// memory, blurred along y at the even rows, then along x at the even
-// columns.
+// REDUCE: a 64 x 16 tile of the destination per 256-thread block. The source
+// footprint (2*16+3 rows x 2*64+3 columns, clamped) is staged in shared
+// memory -- with 16-byte (float) or 8-byte (16-bit) loads of four aligned
+// elements where the four lie inside the row and the plane is aligned, else
+// one element at a time -- then blurred along y at the even rows and along x
+// at the even columns.
 // ---------------------------------------------------------------------------
-constexpr int kPdTW = 32, kPdTH = 8;
-constexpr int kPdSW = 2 * kPdTW + 3;  // source columns 2*x0-2 .. 2*(x0+31)+2
-constexpr int kPdSH = 2 * kPdTH + 3;
+constexpr int kPdTW = 64, kPdTH = 16;
+constexpr int kPdSH = 2 * kPdTH + 3;  // source rows 2*y0-2 .. 2*(y0+15)+2
+constexpr int kPdQ = (2 * kPdTW + 8) / 4;  // groups of four source columns from 2*x0-4
+constexpr int kPdSW = 4 * kPdQ;            // staged columns 2*x0-4 .. 2*x0+131
+
+template <class Ts>
+struct Vec4Of;
+template <>
+struct Vec4Of<float> { using type = float4; };
+template <>
+struct Vec4Of<__nv_bfloat16> { using type = uint2; };
+template <>
+struct Vec4Of<__half> { using type = uint2; };
+
+__device__ __forceinline__ void widen4(const float4& v, float* o) {
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+}
+template <class Ts>
+__device__ __forceinline__ void widen4(const uint2& v, float* o) {
+    const Ts* e = reinterpret_cast<const Ts*>(&v);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) o[k] = to_f32(e[k]);
+}
 
 template <class Ts>
 __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ PyrDownArgs a) {
-    __shared__ float s_src[kPdSH][kPdSW + 1];
+    __shared__ __align__(16) float s_src[kPdSH][kPdSW];
     __shared__ float s_v[kPdTH][kPdSW + 1];
     const int z = blockIdx.z;
     const Ts* __restrict__ src = static_cast<const Ts*>(a.src[z]);
@@ -105,13 +130,25 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ P
     const int hd = (h + 1) >> 1, wd = (w + 1) >> 1;
     const int xd0 = blockIdx.x * kPdTW, yd0 = blockIdx.y * kPdTH;
     if (xd0 >= wd || yd0 >= hd) return;  // a smaller plane of the batch
-    const int sx0 = 2 * xd0 - 2, sy0 = 2 * yd0 - 2;
-    const int tid = threadIdx.y * kPdTW + threadIdx.x;
-    for (int i = tid; i < kPdSH * kPdSW; i += 256) {
-        int r = i / kPdSW, c = i - r * kPdSW;
-        int sy = min(max(sy0 + r, 0), h - 1);
-        int sx = min(max(sx0 + c, 0), w - 1);
-        s_src[r][c] = ld_f32(src + (long long)sy * src_pitch + sx);
+    const int cx0 = 2 * xd0 - 4, sy0 = 2 * yd0 - 2;
+    const int tid = threadIdx.x;
+    // four-element loads need a plane whose rows start on 4-element boundaries
+    const bool vec = ((((uintptr_t)src) & (4 * sizeof(Ts) - 1)) == 0) && (src_pitch & 3) == 0;
+    for (int i = tid; i < kPdSH * kPdQ; i += 256) {
+        const int r = i / kPdQ, q = i - r * kPdQ;
+        const int sy = min(max(sy0 + r, 0), h - 1);
+        const int sx = cx0 + 4 * q;
+        const Ts* row = src + (long long)sy * src_pitch;
+        float* o = &s_src[r][4 * q];
+        if (vec && sx >= 0 && sx + 3 < w) {
+            using V = typename Vec4Of<Ts>::type;
+            const V v = __ldg(reinterpret_cast<const V*>(row + sx));
+            if constexpr (sizeof(Ts) == 4) widen4(v, o);
+            else widen4<Ts>(v, o);
+        } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) o[k] = ld_f32(row + min(max(sx + k, 0), w - 1));
+        }
     }
     __syncthreads();
     const float k0 = 1.0f / 16, k1 = 4.0f / 16, k2 = 6.0f / 16;
@@ -122,12 +159,18 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ P
                     k1 * s_src[sr + 1][c] + k0 * s_src[sr + 2][c];
     }
     __syncthreads();
-    int xd = xd0 + threadIdx.x, yd = yd0 + threadIdx.y;
-    if (xd < wd && yd < hd) {
-        int c = 2 * threadIdx.x + 2;
-        const float* v = s_v[threadIdx.y];
-        dst[(long long)yd * dst_pitch + xd] =
-            from_f32<Ts>(k0 * v[c - 2] + k1 * v[c - 1] + k2 * v[c] + k1 * v[c + 1] + k0 * v[c + 2]);
+    const int x = tid & (kPdTW - 1);
+    const int xd = xd0 + x;
+    if (xd < wd) {
+        const int c = 2 * x + 4;  // staged column of source column 2 * xd
+#pragma unroll
+        for (int r = tid / kPdTW; r < kPdTH; r += 256 / kPdTW) {
+            const int yd = yd0 + r;
+            if (yd >= hd) break;
+            const float* v = s_v[r];
+            dst[(long long)yd * dst_pitch + xd] =
+                from_f32<Ts>(k0 * v[c - 2] + k1 * v[c - 1] + k2 * v[c] + k1 * v[c + 1] + k0 * v[c + 2]);
+        }
     }
 }
 
@@ -158,7 +201,7 @@ cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s) {
         hd = max(hd, (a.h[i] + 1) / 2);
         wd = max(wd, (a.w[i] + 1) / 2);
     }
-    dim3 block(kPdTW, kPdTH);
+    dim3 block(256);
     dim3 grid((wd + kPdTW - 1) / kPdTW, (hd + kPdTH - 1) / kPdTH, a.count);
     switch (a.pyr) {
         case kPyrF32: pyr_down_kernel<float><<<grid, block, 0, s>>>(a); break;

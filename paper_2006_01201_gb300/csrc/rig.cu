@@ -33,6 +33,15 @@ struct GraphKey {
     unsigned long long tune_gen;
 };
 
+// A captured graph and what it was captured for.
+struct GraphSlot {
+    GraphKey key;
+    cudaGraphExec_t exec;
+    int kernels;
+    unsigned long long last_use;
+};
+constexpr int kGraphSlots = 4;  // e.g. the buffer sets of a double-buffered pipeline
+
 struct RunCall {
     const pano_image* L;
     const pano_image* R;
@@ -63,9 +72,8 @@ struct pano_rig {
     pano_rig_tuning tune[kMaxLevels];
     unsigned long long tune_gen;
     cudaStream_t cap_stream;
-    cudaGraphExec_t exec;
-    GraphKey key;
-    int graph_kernels;
+    GraphSlot graphs[kGraphSlots];
+    unsigned long long graph_clock;
     int captures;
     unsigned long long launches;
     Trace tr;
@@ -344,37 +352,40 @@ GraphKey make_key(const pano_rig* r, const RunCall& c) {
     return k;
 }
 
-pano_status capture(pano_rig* r, const RunCall& c) {
-    if (r->exec) {
-        cudaGraphExecDestroy(r->exec);
-        r->exec = nullptr;
+// Capture the call's launch sequence into slot `g` (replacing its graph).
+pano_status capture(pano_rig* r, const RunCall& c, int g) {
+    GraphSlot& slot = r->graphs[g];
+    if (slot.exec) {
+        cudaGraphExecDestroy(slot.exec);
+        slot.exec = nullptr;
     }
     cudaError_t e = cudaStreamBeginCapture(r->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
     int kernels = 0;
     cudaError_t le = enqueue_all(r, c, r->cap_stream, false, &kernels);
-    cudaGraph_t g = nullptr;
-    e = cudaStreamEndCapture(r->cap_stream, &g);  // always ends the capture
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(r->cap_stream, &graph);  // always ends the capture
     if (le != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
+        if (graph) cudaGraphDestroy(graph);
         return cuda_fail(le, "launch during graph capture");
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&r->exec, g, 0);
-    cudaGraphDestroy(g);
+    e = cudaGraphInstantiate(&slot.exec, graph, 0);
+    cudaGraphDestroy(graph);
     if (e != cudaSuccess) {
-        r->exec = nullptr;
+        slot.exec = nullptr;
         return cuda_fail(e, "cudaGraphInstantiate");
     }
-    r->key = make_key(r, c);
-    r->graph_kernels = kernels;
+    slot.key = make_key(r, c);
+    slot.kernels = kernels;
     r->captures++;
     return PANO_OK;
 }
 
 void free_rig(pano_rig* r) {
     trace_free(r->tr);
-    if (r->exec) cudaGraphExecDestroy(r->exec);
+    for (GraphSlot& g : r->graphs)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     if (r->cap_stream) cudaStreamDestroy(r->cap_stream);
     if (r->buf) cudaFree(r->buf);
     delete r;
@@ -518,13 +529,26 @@ pano_status pano_rig_run(pano_rig* r, const pano_image* L, const pano_image* R, 
         r->launches += kernels;
         return e == cudaSuccess ? PANO_OK : cuda_fail(e, "rig launch");
     }
+    // a graph captured for these pointers, pitches and tuning, else a new
+    // capture in the least recently used slot
     GraphKey k = make_key(r, c);
-    if (!r->exec || memcmp(&k, &r->key, sizeof(k)) != 0) {
-        if ((st = capture(r, c)) != PANO_OK) return st;
+    int g = -1, lru = 0;
+    for (int i = 0; i < kGraphSlots; ++i) {
+        if (r->graphs[i].exec && memcmp(&k, &r->graphs[i].key, sizeof(k)) == 0) g = i;
+        if (!r->graphs[i].exec) {
+            if (r->graphs[lru].exec) lru = i;
+        } else if (r->graphs[lru].exec && r->graphs[i].last_use < r->graphs[lru].last_use) {
+            lru = i;
+        }
     }
-    cudaError_t e = cudaGraphLaunch(r->exec, s);
+    if (g < 0) {
+        g = lru;
+        if ((st = capture(r, c, g)) != PANO_OK) return st;
+    }
+    r->graphs[g].last_use = ++r->graph_clock;
+    cudaError_t e = cudaGraphLaunch(r->graphs[g].exec, s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
-    r->launches += r->graph_kernels;
+    r->launches += r->graphs[g].kernels;
     return PANO_OK;
 }
 

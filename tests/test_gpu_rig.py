@@ -141,6 +141,12 @@ def test_graph_replay_equals_eager_and_recaptures_on_new_buffers(small_rig_pairs
         c_other = rig.new_canvas()
         rig.run(Ls, Rs, canvas=c_other, use_graph=True)  # new canvas pointer: new graph
         assert rig.graph_captures == 2
+        for _ in range(3):                                # both graphs stay cached
+            rig.run(Ls, Rs, canvas=c_graph, use_graph=True)
+            rig.run(Ls, Rs, canvas=c_other, use_graph=True)
+        assert rig.graph_captures == 2
+        torch.cuda.synchronize()
+        assert torch.equal(c_graph, c_other)
         rig.set_tuning(0, binding.PANO_LK_TILE, tile_w=32, tile_h=8)
         rig.run(Ls, Rs, canvas=c_other, use_graph=True)  # new tuning: new graph
         assert rig.graph_captures == 3
@@ -151,6 +157,40 @@ def test_graph_replay_equals_eager_and_recaptures_on_new_buffers(small_rig_pairs
                                              (binding.PANO_LK_STREAM, 64, (0, 0)),
                                              (binding.PANO_LK_TILE, 0, (64, 8)),
                                              (binding.PANO_LK_TILE, 0, (16, 16))])
+def test_host_pipeline_matches_direct_calls(small_rig_pairs):
+    """Double-buffered host pipelines (copies of neighbouring items overlap
+    the kernels of the current one) give the results of direct calls."""
+    pairs = small_rig_pairs
+    with make_rig(pairs) as rig:
+        Ls, Rs = [cuda(p.L) for p in pairs], [cuda(p.R) for p in pairs]
+        ref = rig.new_canvas()
+        rig.run(Ls, Rs, canvas=ref, use_graph=True)
+        torch.cuda.synchronize()
+        pipe = binding.RigHostPipeline(rig)
+        Lh = [torch.from_numpy(p.L).pin_memory() for p in pairs]
+        Rh = [torch.from_numpy(p.R).pin_memory() for p in pairs]
+        outs = [torch.empty(tuple(ref.shape), dtype=ref.dtype).pin_memory() for _ in range(4)]
+        for k in range(4):
+            pipe.submit(k, Lh, Rh, outs[k])
+        pipe.drain()
+        for o in outs:
+            assert torch.equal(o, ref.cpu())
+        assert rig.graph_captures <= 3
+    p = pairs[0]
+    h, w = p.L.shape[:2]
+    with binding.FlowContext(binding.Params(levels=GEOM["levels"]), h, w, 3) as ctx:
+        _, _, F = ctx.stitch_pair(cuda(p.L), cuda(p.R))
+        torch.cuda.synchronize()
+        pipe = ctx.host_pipeline(p.L.shape, torch.uint8)
+        Lh, Rh = torch.from_numpy(p.L).pin_memory(), torch.from_numpy(p.R).pin_memory()
+        outs = [torch.empty(p.L.shape, dtype=torch.uint8).pin_memory() for _ in range(3)]
+        for k in range(3):
+            pipe.submit(k, Lh, Rh, outs[k])
+        pipe.drain()
+        for o in outs:
+            assert torch.equal(o, F.cpu())
+
+
 def test_forced_kernels_agree_with_default(small_rig_pairs, kernel, seg, tile):
     pairs = small_rig_pairs
     Ls, Rs = [cuda(p.L) for p in pairs], [cuda(p.R) for p in pairs]
