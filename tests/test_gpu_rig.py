@@ -153,10 +153,6 @@ def test_graph_replay_equals_eager_and_recaptures_on_new_buffers(small_rig_pairs
         torch.cuda.synchronize()
 
 
-@pytest.mark.parametrize("kernel,seg,tile", [(binding.PANO_LK_STREAM, 0, (0, 0)),
-                                             (binding.PANO_LK_STREAM, 64, (0, 0)),
-                                             (binding.PANO_LK_TILE, 0, (64, 8)),
-                                             (binding.PANO_LK_TILE, 0, (16, 16))])
 def test_host_pipeline_matches_direct_calls(small_rig_pairs):
     """Double-buffered host pipelines (copies of neighbouring items overlap
     the kernels of the current one) give the results of direct calls."""
@@ -191,6 +187,10 @@ def test_host_pipeline_matches_direct_calls(small_rig_pairs):
             assert torch.equal(o, F.cpu())
 
 
+@pytest.mark.parametrize("kernel,seg,tile", [(binding.PANO_LK_STREAM, 0, (0, 0)),
+                                             (binding.PANO_LK_STREAM, 64, (0, 0)),
+                                             (binding.PANO_LK_TILE, 0, (64, 8)),
+                                             (binding.PANO_LK_TILE, 0, (16, 16))])
 def test_forced_kernels_agree_with_default(small_rig_pairs, kernel, seg, tile):
     pairs = small_rig_pairs
     Ls, Rs = [cuda(p.L) for p in pairs], [cuda(p.R) for p in pairs]
