@@ -16,12 +16,28 @@ namespace pano {
 
 namespace {
 
+// A stored sample as float. A byte b becomes exactly b through the float
+// whose bits are those of 2^23 with b in the low mantissa bits, minus 2^23:
+// one logic operation and one add instead of an integer-to-float conversion.
+__device__ __forceinline__ float sample_f(float v) { return v; }
+__device__ __forceinline__ float sample_f(uint8_t b) {
+    return __uint_as_float(0x4B000000u | (unsigned)b) - 8388608.0f;
+}
+
+// round(f) to [0, 255], ties to even: after clamping, f + 2^23 is rounded by
+// the add to the nearest integer (ties to even) and that integer is the low
+// mantissa byte. Clamping first gives what rounding and then clamping gives.
+__device__ __forceinline__ uint8_t to_u8_rn(float f) {
+    f = fminf(fmaxf(f, 0.f), 255.f);  // a NaN becomes 0
+    return (uint8_t)(__float_as_uint(f + 8388608.0f) & 0xFFu);
+}
+
 // Bilinear sample of channel k of an interleaved image, raw sample scale
 // (0..255 for u8, as stored for f32).
 template <typename Tv>
 __device__ __forceinline__ float sample_channel(const Tv* __restrict__ base, const Taps& t, int k) {
-    return bilinear_mix(t, (float)base[t.o00 + k], (float)base[t.o10 + k], (float)base[t.o01 + k],
-                        (float)base[t.o11 + k]);
+    return bilinear_mix(t, sample_f(base[t.o00 + k]), sample_f(base[t.o10 + k]), sample_f(base[t.o01 + k]),
+                        sample_f(base[t.o11 + k]));
 }
 
 // F at strip pixel (x, y), stored at column `fx` of row y of a.F.
@@ -29,15 +45,15 @@ template <typename Tv, int C>
 __device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y, int fx) {
     const int w = a.L.w, h = a.L.h;
     const long long p = (long long)y * w + x;
-    const float B = a.blend ? a.blend[p] : (float)(x + 1) / (float)(w + 1);
+    const float B = a.blend ? a.blend[p] : (float)(x + 1) * a.inv_w1;
     const float2 rl = a.flowRL[p], lr = a.flowLR[p];
     const float blendL = 1.f - B, blendR = B;
     // ColorL at p + (1 - BlendL) FlowRtoL, ColorR at p + (1 - BlendR) FlowLtoR
     const int pitchL = (int)(a.L.pitch_bytes / sizeof(Tv)), pitchR = (int)(a.R.pitch_bytes / sizeof(Tv));
     const Taps tl = bilinear_taps(x, y, (1.f - blendL) * rl.x, (1.f - blendL) * rl.y, w, h, pitchL, C);
     const Taps tr = bilinear_taps(x, y, (1.f - blendR) * lr.x, (1.f - blendR) * lr.y, w, h, pitchR, C);
-    const float magRL = sqrtf(fmaf(rl.x, rl.x, rl.y * rl.y)) / (float)w;
-    const float magLR = sqrtf(fmaf(lr.x, lr.x, lr.y * lr.y)) / (float)w;
+    const float magRL = sqrtf(fmaf(rl.x, rl.x, rl.y * rl.y)) * a.inv_w;
+    const float magLR = sqrtf(fmaf(lr.x, lr.x, lr.y * lr.y)) * a.inv_w;
     const float sL = a.k_sharp * blendL * fmaf(a.k_mag, magRL, 1.f);
     const float sR = a.k_sharp * blendR * fmaf(a.k_mag, magLR, 1.f);
     const float e = expf(fminf(fmaxf(sR - sL, -80.f), 80.f));
@@ -52,7 +68,7 @@ __device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y, in
         const float cr = sample_channel(Rb, tr, k);
         const float f = fmaf(cl, wL, cr * wR);
         if constexpr (sizeof(Tv) == 1) {
-            out[k] = (Tv)min(max(__float2int_rn(f), 0), 255);
+            out[k] = to_u8_rn(f);
         } else {
             out[k] = (Tv)f;
         }
@@ -101,13 +117,15 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
     const Taps t = bilinear_taps(x, y, a.scale * f.x, a.scale * f.y, w, h, pitch, C);
     const Tv* __restrict__ base = static_cast<const Tv*>(a.src.data);
     float* out = reinterpret_cast<float*>(reinterpret_cast<char*>(a.dst) + (long long)y * a.dst_pitch_bytes) + x * C;
-    const float scale = sizeof(Tv) == 1 ? 1.0f / 255.0f : 1.0f;
+    const float scale = sizeof(Tv) == 1 ? 1.0f / 255.0f : 1.0f;  // samples widened by sample_f
     for (int k = 0; k < C; ++k) out[k] = sample_channel(base, t, k) * scale;
 }
 
 }  // namespace
 
-cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
+cudaError_t launch_blend(const BlendArgs& args, cudaStream_t s) {
+    BlendArgs a = args;
+    set_blend_scales(&a);
     dim3 block(32, 8);
     dim3 grid((a.L.w + 31) / 32, (a.L.h + 7) / 8);
     if (a.L.dtype == 0) {
@@ -120,8 +138,10 @@ cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_rig_blend(const RigBlendArgs& r, cudaStream_t s) {
-    if (r.n < 1 || r.n > kMaxBatch) return cudaErrorInvalidValue;
+cudaError_t launch_rig_blend(const RigBlendArgs& args, cudaStream_t s) {
+    if (args.n < 1 || args.n > kMaxBatch) return cudaErrorInvalidValue;
+    RigBlendArgs r = args;
+    for (int p = 0; p < r.n; ++p) set_blend_scales(&r.pair[p]);
     int h = 0, w = 0;
     for (int p = 0; p < r.n; ++p) {
         h = max(h, r.pair[p].L.h);

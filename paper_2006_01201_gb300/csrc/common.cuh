@@ -163,7 +163,14 @@ struct BlendArgs {
     void* F;
     long long F_pitch_bytes;
     float k_sharp, k_mag;
+    float inv_w, inv_w1;  // 1 / w and 1 / (w + 1), rounded to nearest (the launchers set them)
 };
+
+// The reciprocals a blend launch multiplies by instead of dividing.
+inline void set_blend_scales(BlendArgs* a) {
+    a->inv_w = 1.0f / (float)a->L.w;
+    a->inv_w1 = 1.0f / (float)(a->L.w + 1);
+}
 
 // Blend of every pair of a rig into one canvas (F of each pair is the canvas
 // row of strip row 0; the column comes from x0).

@@ -19,13 +19,17 @@ constexpr float kInv255 = 1.0f / 255.0f;
 // in one launch (blockIdx.z selects the strip; the grid-constant descriptor
 // is indexed in parameter space, without a local copy).
 // ---------------------------------------------------------------------------
+// A byte value as float, exactly: the bits of 2^23 with the byte in the low
+// mantissa bits, minus 2^23 (no integer-to-float conversion).
+__device__ __forceinline__ float byte_f(uint32_t b) { return __uint_as_float(0x4B000000u | b) - 8388608.0f; }
+
 __device__ __forceinline__ float luma_at(const ImageDesc& in, const unsigned char* row, int x) {
     if (in.dtype == 0) {
         if (in.c == 3) {
             const uint8_t* px = row + 3 * x;
-            return (0.299f * px[0] + 0.587f * px[1] + 0.114f * px[2]) * kInv255;
+            return (0.299f * byte_f(px[0]) + 0.587f * byte_f(px[1]) + 0.114f * byte_f(px[2])) * kInv255;
         }
-        return row[x] * kInv255;
+        return byte_f(row[x]) * kInv255;
     }
     const float* r = reinterpret_cast<const float*>(row);
     if (in.c == 3) return 0.299f * r[3 * x] + 0.587f * r[3 * x + 1] + 0.114f * r[3 * x + 2];
@@ -75,7 +79,7 @@ __global__ void __launch_bounds__(256) luma_kernel(const __grid_constant__ LumaA
                                 w2 & 255, (w2 >> 8) & 255, (w2 >> 16) & 255, w2 >> 24};
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-            v[k] = (0.299f * (float)b[3 * k] + 0.587f * (float)b[3 * k + 1] + 0.114f * (float)b[3 * k + 2]) * kInv255;
+            v[k] = (0.299f * byte_f(b[3 * k]) + 0.587f * byte_f(b[3 * k + 1]) + 0.114f * byte_f(b[3 * k + 2])) * kInv255;
         store4(orow + x, v);
         return;
     }
