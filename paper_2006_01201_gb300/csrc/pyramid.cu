@@ -15,7 +15,8 @@ namespace {
 constexpr float kInv255 = 1.0f / 255.0f;
 
 // ---------------------------------------------------------------------------
-// Level 0: each thread converts 4 consecutive pixels of one row. All strips
+// Level 0: each thread converts 4 consecutive pixels of one row, a block
+// 256 x 4 pixels. All strips
 // in one launch (blockIdx.z selects the strip; the grid-constant descriptor
 // is indexed in parameter space, without a local copy).
 // ---------------------------------------------------------------------------
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(256) luma_kernel(const __grid_constant__ LumaA
     To* out = static_cast<To*>(a.out[blockIdx.z]);
     const int out_pitch = a.out_pitch[blockIdx.z];
     const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = blockIdx.y;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= in.w || y >= in.h) return;
     const unsigned char* row = static_cast<const unsigned char*>(in.data) + (long long)y * in.pitch_bytes;
     To* orow = out + (long long)y * out_pitch;
@@ -187,8 +188,9 @@ cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s) {
         h = max(h, a.in[i].h);
         w = max(w, a.in[i].w);
     }
-    dim3 block(64);
-    dim3 grid((w + 4 * 64 - 1) / (4 * 64), h, a.count);
+    // 64 x 4 threads, four pixels each: 256 x 4 pixels per block
+    dim3 block(64, 4);
+    dim3 grid((w + 4 * 64 - 1) / (4 * 64), (h + 3) / 4, a.count);
     switch (a.pyr) {
         case kPyrF32: luma_kernel<float><<<grid, block, 0, s>>>(a); break;
         case kPyrBF16: luma_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(a); break;
