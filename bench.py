@@ -41,7 +41,7 @@ SMALL_TILE_PIXELS = 16000    # tiled levels below this many pixels use 16 x 8 ti
 # DRAM bytes (read + write) per launch of the dominant kernel, averaged over
 # its launches in one step, from an ncu capture of the current kernel; None
 # when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (171.411968e6 + 4.652544e6 + 18.478336e6) / 3}
+TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (1.188352e6 + 4.644352e6 + 18.4704e6 + 171.916032e6) / 4}
 
 
 # ---------------------------------------------------------------------------
