@@ -35,6 +35,9 @@ METRIC = "overlap megapixels/sec (bi-flow+warp+blend) on 1 GB300; % HBM roofline
 UNIT = "MP/s"
 WORKLOAD = {"workload": "pair_4000x1500_rgb_u8_lv6", "h": 4000, "w": 1500, "channels": 3, "levels": 6,
             "iters": 5, "radius": 2}
+# the small single-pair configuration: launch-latency bound, reported, not the headline
+SMALL_WORKLOAD = {"workload": "pair_256x512_gray_f32_lv4", "h": 256, "w": 512, "channels": 1, "levels": 4,
+                  "iters": 5, "radius": 2}
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 STREAM_MIN_PIXELS = 50000    # levels with at least this many pixels use the streamed LK kernel
 SMALL_TILE_PIXELS = 16000    # tiled levels below this many pixels use 16 x 8 tiles
@@ -120,6 +123,12 @@ def rig_level_kernels(h: int, widths, levels: int, kernels, tiles=None):
             lev.append(("lk_level_batch_kernel", members))
         out.append(lev)
     return out
+
+
+def unfused_stage_bytes(h: int, w: int, levels: int, iters: int, elem: int = 4) -> int:
+    """Bytes if every LK step were its own pass: per direction, step and level
+    pixel read u, T, J and write u (8 + 2 elem + 8 B)."""
+    return sum(2 * iters * (16 + 2 * elem) * n for n in level_pixels(h, w, levels))
 
 
 def throughput(pixels_per_step: int, steps: int, world: int, max_total_ms: float) -> float:
@@ -238,6 +247,56 @@ def time_oracle(pair, levels: int, budget_s: float, band_rows: int = 500, max_ba
     return done_px / t_total / 1e6, oracle.num_threads(), desc, t_total
 
 
+def cpu_model() -> str:
+    """The host CPU as /proc/cpuinfo names it (model name, else implementer/part)."""
+    try:
+        info = open("/proc/cpuinfo").read()
+    except OSError:
+        return "unknown"
+    for key in ("model name", "Model"):
+        for line in info.splitlines():
+            if line.startswith(key):
+                return line.split(":", 1)[1].strip()
+    fields = {}
+    for line in info.splitlines():
+        if ":" in line:
+            k, v = (x.strip() for x in line.split(":", 1))
+            fields.setdefault(k, v)
+    return f"implementer {fields.get('CPU implementer', '?')} part {fields.get('CPU part', '?')}"
+
+
+def oracle_baseline(pair, levels: int, budget_s: float, label: str):
+    """cpu_baseline object: the oracle on all host cores (the value) and on
+    one thread (reported beside it), on row bands of the pair."""
+    import oracle
+    v, cores, desc, secs = time_oracle(pair, levels, budget_s=budget_s)
+    nthreads = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        v1, _, desc1, secs1 = time_oracle(pair, levels, budget_s=budget_s / 4, band_rows=100)
+    finally:
+        oracle.set_num_threads(nthreads)
+    return {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc.replace("of the pair", label),
+            "seconds": secs, "single_thread": {"value": v1, "sample": desc1.replace("of the pair", label),
+                                               "seconds": secs1},
+            "cpu": cpu_model(), "nproc": os.cpu_count()}
+
+
+# The paper's own figure (whole workflow, one 9000x4000 panorama, GPU model
+# not stated): context for the rig numbers, not a target.
+PAPER_CONTEXT = "under 30 s per 9000x4000 panorama for the whole workflow on an unspecified GPU (Sections I and V)"
+
+# FP32 arithmetic of one LK step per level pixel: bilinear sample 8, It 1,
+# products 2, separable box sums 8, 2x2 solve 12, update 2, plus gradient
+# and normal matrices amortised (about 50 in all).
+LK_FLOPS_PER_PIXEL_STEP = 50
+
+
+def fp32_peak_tflops(sm_mhz: float = 2070.0, sms: int = 152) -> float:
+    """FP32 FMA peak: 128 lanes per SM, 2 flops per FMA."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def time_pipeline(pipe, submit, steps: int, world: int, repeats: int = 3):
     """Milliseconds from before the first upload to after the last download of
     `steps` items submitted to a host pipeline (max over ranks), measured
@@ -308,10 +367,14 @@ def run_gpu(args):
 
     gpu_build.build()
     pkg.load_library()
-    h, w, c, levels = WORKLOAD["h"], WORKLOAD["w"], WORKLOAD["channels"], WORKLOAD["levels"]
-    pair = synth.pair_fullres_rgb(seed=1 + rank, h=h, w=w, levels=levels)
+    WL = SMALL_WORKLOAD if args.workload == "small" else WORKLOAD
+    h, w, c, levels = WL["h"], WL["w"], WL["channels"], WL["levels"]
+    if args.workload == "small":
+        pair = synth.pair_small_gray(seed=rank, h=h, w=w, levels=levels)
+    else:
+        pair = synth.pair_fullres_rgb(seed=1 + rank, h=h, w=w, levels=levels)
     pyr_code, pyr_fmt, elem = PYR_DTYPES[args.pyr_dtype]
-    ctx = pkg.FlowContext(pkg.Params(levels=levels, iters=WORKLOAD["iters"], radius=WORKLOAD["radius"],
+    ctx = pkg.FlowContext(pkg.Params(levels=levels, iters=WL["iters"], radius=WL["radius"],
                                      pyr_dtype=pyr_code),
                           max_h=h, max_w=w, max_c=c)
     L = torch.from_numpy(pair.L).to(dev)
@@ -396,6 +459,8 @@ def run_gpu(args):
                 "launches_per_step": launches_per_step, "peak_source": f"{peak_src} hbm_gbs"}
     path_bytes = path_alg_bytes(h, w, c, levels, elem=elem)
     path_gbs = path_bytes / (total_ms / args.steps * 1e-3) / 1e9
+    stage_bytes = unfused_stage_bytes(h, w, levels, WL["iters"], elem)
+    path_flops = 2 * WL["iters"] * LK_FLOPS_PER_PIXEL_STEP * sum(level_pixels(h, w, levels))
 
     # --- end to end: pinned host strips in, F back to pinned host memory,
     #     through the library's double-buffered host pipeline (the copies of
@@ -419,10 +484,16 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": dict(WORKLOAD, l2="flushed between steps (256 MB write, untimed)",
+                "config": dict(WL, l2="flushed between steps (256 MB write, untimed)",
                                parallelism=f"replicas{world}", pyr_dtype=args.pyr_dtype),
                 "roofline": roofline,
-                "path": {"alg_bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / peak},
+                "path": {"alg_bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / peak,
+                         "unfused_stage_bytes_per_step": stage_bytes,
+                         "fp32_tflops": path_flops / (total_ms / args.steps * 1e-3) / 1e12,
+                         "fp32_peak_tflops": fp32_peak_tflops(clocks["sm_mhz"] if clocks else 2070.0),
+                         "fp32_frac": path_flops / (total_ms / args.steps * 1e-3) / 1e12
+                         / fp32_peak_tflops(clocks["sm_mhz"] if clocks else 2070.0),
+                         "flops_per_step": path_flops},
                 "kernels": per_kind, "dominant_kernel": dominant,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
@@ -437,12 +508,20 @@ def run_gpu(args):
             e_lr = float(np.hypot(*(g_lr - olr).transpose(2, 0, 1)).mean())
             e_rl = float(np.hypot(*(g_rl - orl).transpose(2, 0, 1)).mean())
             line["epe_vs_oracle"] = {"LtoR_mean_px": e_lr, "RtoL_mean_px": e_rl}
+            Fo = oracle.blend(pair.L, pair.R, olr, orl, oracle.Params(levels=levels))
+            if pair.L.dtype == np.uint8:
+                dF = np.abs(F.cpu().numpy().astype(int) - oracle.quantize_u8(Fo).astype(int))
+                line["F_u8_vs_oracle"] = {"max_lsb": int(dF.max()), "mean_lsb": float(dF.mean()),
+                                          "frac_gt_1lsb": float((dF > 1).mean())}
+            else:
+                dF = np.abs(F.cpu().numpy().astype(np.float64) - Fo)
+                line["F_vs_oracle"] = {"max_abs": float(dF.max()), "mean_abs": float(dF.mean()),
+                                       "max_in_u8_lsb": float(dF.max() * 255)}
             if pyr_fmt:
                 line["half_precision"] = half_precision_report(pkg, pair, levels, pyr_fmt, g_lr, g_rl,
                                                                F.cpu().numpy(), olr, orl, dev)
-            v, cores, desc, secs = time_oracle(pair, levels, budget_s=args.cpu_budget)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
-                                    "seconds": secs, "full_pair_flow_s": t_full}
+            line["cpu_baseline"] = oracle_baseline(pair, levels, args.cpu_budget, f"of the {h}x{w} pair")
+            line["cpu_baseline"]["full_pair_flow_s"] = t_full
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -790,6 +869,7 @@ def run_rig(args):
                 "single_pair_form": {"value": throughput(npx, args.steps, world, pair_ms), "unit": UNIT,
                                      "ms_per_step": pair_ms / args.steps},
                 "fp32_batched_form": fp32_form,
+                "paper_context": PAPER_CONTEXT,
                 "autotune": {"seconds": tune_s, "levels": tunings},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
@@ -815,10 +895,8 @@ def run_rig(args):
                 line["half_precision"]["canvas_u8_vs_fp32_rig"] = {
                     "max_lsb": int((canvas.int() - canvas32.int()).abs().max()),
                     "mean_lsb": float((canvas.int() - canvas32.int()).abs().float().mean())}
-            v, cores, desc, secs = time_oracle(pairs[0], levels, budget_s=args.cpu_budget)
-            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                    "sample": desc.replace("of the pair", "of rig pair 0 (4000x800)"),
-                                    "seconds": secs}
+            line["cpu_baseline"] = oracle_baseline(pairs[0], levels, args.cpu_budget, "of rig pair 0 (4000x800)")
+            line["cpu_baseline"]["rig_step_s_extrapolated"] = npx / 1e6 / line["cpu_baseline"]["value"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     rig.close()
@@ -836,9 +914,10 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="pair", choices=["pair", "rig", "refine_1024", "blend_coeff"],
-                    help="pair: the 4000x1500 overlap pair (default); rig: the 8-pair 360-degree rig; "
-                         "refine_1024: the differentiable refinement; blend_coeff: general-mask Eq. (1)")
+    ap.add_argument("--workload", default="pair", choices=["pair", "small", "rig", "refine_1024", "blend_coeff"],
+                    help="pair: the 4000x1500 overlap pair (default); small: the 256x512 gray pair; "
+                         "rig: the 8-pair 360-degree rig; refine_1024: the differentiable refinement; "
+                         "blend_coeff: general-mask Eq. (1)")
     ap.add_argument("--no-autotune", action="store_true", help="rig: keep the default tuning")
     ap.add_argument("--pyr-dtype", default="f32", choices=sorted(PYR_DTYPES),
                     help="storage of the pyramid levels (arithmetic stays FP32)")
