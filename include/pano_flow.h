@@ -247,6 +247,7 @@ PANO_API pano_status pano_flow_pair_static(const pano_flow_params* params, const
 #define PANO_TRACE_PYR_DOWN 0x2u   /* pyramid REDUCE */
 #define PANO_TRACE_LK       0x4u   /* one Lucas-Kanade level, both directions */
 #define PANO_TRACE_BLEND    0x8u   /* Code 1 blend */
+#define PANO_TRACE_LUMA_REDUCE 0x10u  /* level 0 (luma) and level 1 (its REDUCE) in one launch */
 
 typedef struct pano_trace_record {
     int kind;     /* one PANO_TRACE_* bit */
@@ -278,6 +279,13 @@ PANO_API unsigned long long pano_flow_launches(const pano_flow_ctx* ctx);
 /* Level 0 of the pyramid: unit-scaled luma Y (h x w) of an image (BT.601
  * for c = 3, the sample itself for c = 1). Y pitch >= w. */
 PANO_API pano_status pano_stage_luma(const pano_image* in, float* Y, int y_pitch, void* cuda_stream);
+
+/* Level 0 and level 1 of the pyramid in one launch, as pano_flow_pair forms
+ * them: Y as pano_stage_luma writes it (h x w) and Y1 its REDUCE as
+ * pano_stage_pyr_down writes it (ceil(h/2) x ceil(w/2)), bit for bit.
+ * Pitches in floats. */
+PANO_API pano_status pano_stage_luma_pyr(const pano_image* in, float* Y, int y_pitch, float* Y1, int y1_pitch,
+                                         void* cuda_stream);
 
 /* One pyramid REDUCE step (Section III-C-1, "LK pyramid"): [1 4 6 4 1]/16
  * along y then x, replicate border, keep even rows and columns.

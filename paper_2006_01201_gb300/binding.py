@@ -69,6 +69,7 @@ _PAR = ctypes.POINTER(PanoParams)
 _PP = ctypes.POINTER(ctypes.c_void_p)
 
 PANO_TRACE_LUMA, PANO_TRACE_PYR_DOWN, PANO_TRACE_LK, PANO_TRACE_BLEND = 0x1, 0x2, 0x4, 0x8
+PANO_TRACE_LUMA_REDUCE = 0x10
 
 SIGNATURES = {
     "pano_flow_params_default": ([_PAR], None),
@@ -85,6 +86,7 @@ SIGNATURES = {
     "pano_stage_pyr_down_adjoint": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
     "pano_stage_luma": ([_IMG, _VP, _I, _VP], _I),
     "pano_stage_pyr_down": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
+    "pano_stage_luma_pyr": ([_IMG, _VP, _I, _VP, _I, _VP], _I),
     "pano_stage_lk": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _VP], _I),
     "pano_stage_warp": ([_IMG, _VP, _F, _IMG, _VP], _I),
     "pano_blend_coeff_scratch_bytes": ([_I, _I], ctypes.c_size_t),
@@ -627,6 +629,17 @@ def stage_luma(img, stream=None):
     Y = torch.empty((d.h, d.w), dtype=torch.float32, device=img.device)
     _check(load_library().pano_stage_luma(ctypes.byref(d), Y.data_ptr(), d.w, _stream_ptr(stream)))
     return Y
+
+
+def stage_luma_pyr(img, stream=None):
+    """(level 0, level 1) of an image in one launch, as the flow path forms them."""
+    torch = _torch()
+    d = image_desc(img)
+    Y = torch.empty((d.h, d.w), dtype=torch.float32, device=img.device)
+    Y1 = torch.empty(((d.h + 1) // 2, (d.w + 1) // 2), dtype=torch.float32, device=img.device)
+    _check(load_library().pano_stage_luma_pyr(ctypes.byref(d), Y.data_ptr(), d.w, Y1.data_ptr(), Y1.shape[1],
+                                              _stream_ptr(stream)))
+    return Y, Y1
 
 
 def stage_pyr_down(src, stream=None):

@@ -265,13 +265,32 @@ void pair_planes(const pano_flow_ctx* c, const pano_image* L, const pano_image* 
 
 cudaError_t launch_pair_pyramid(pano_flow_ctx* c, const PairPlanes& pp, cudaStream_t s) {
     cudaError_t e;
-    if (pp.luma.count > 0) {
+    int first = 1;  // first level left to REDUCE
+    if (pp.luma.count == 2 && c->nlev >= 2) {
+        // level 0 and level 1 of both strips in one launch
+        LumaReduceArgs lr;
+        memset(&lr, 0, sizeof(lr));
+        for (int i = 0; i < 2; ++i) {
+            lr.in[i] = pp.luma.in[i];
+            lr.l0[i] = pp.luma.out[i];
+            lr.l0_pitch[i] = pp.luma.out_pitch[i];
+            lr.l1[i] = c->pyr[i][1];
+            lr.l1_pitch[i] = c->lev_pitch[1];
+        }
+        lr.count = 2;
+        lr.pyr = pp.luma.pyr;
+        int t = trace_begin(c->tr, PANO_TRACE_LUMA_REDUCE, 1, s);
+        if ((e = launch_luma_reduce(lr, s)) != cudaSuccess) return e;
+        trace_end(c->tr, t, s);
+        c->launches++;
+        first = 2;
+    } else if (pp.luma.count > 0) {
         int t = trace_begin(c->tr, PANO_TRACE_LUMA, 0, s);
         if ((e = launch_luma(pp.luma, s)) != cudaSuccess) return e;
         trace_end(c->tr, t, s);
         c->launches++;
     }
-    for (int l = 1; l < c->nlev; ++l) {
+    for (int l = first; l < c->nlev; ++l) {
         PyrDownArgs pa;
         memset(&pa, 0, sizeof(pa));
         for (int si = 0; si < 2; ++si) {
@@ -493,6 +512,26 @@ pano_status pano_stage_luma(const pano_image* in, float* Y, int y_pitch, void* c
     la.count = 1;
     cudaError_t e = launch_luma(la, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? PANO_OK : cuda_fail(e, "luma launch");
+}
+
+pano_status pano_stage_luma_pyr(const pano_image* in, float* Y, int y_pitch, float* Y1, int y1_pitch,
+                                void* cuda_stream) {
+    pano_status st;
+    if ((st = check_image(in, "in")) != PANO_OK) return st;
+    if (!Y || !Y1 || ((uintptr_t)Y) % 4 || ((uintptr_t)Y1) % 4)
+        return fail(PANO_ERR_INVALID_ARG, "Y or Y1 is NULL or misaligned");
+    if (y_pitch < in->w || y1_pitch < (in->w + 1) / 2)
+        return fail(PANO_ERR_INVALID_ARG, "y_pitch %d or y1_pitch %d too small", y_pitch, y1_pitch);
+    LumaReduceArgs lr;
+    memset(&lr, 0, sizeof(lr));
+    lr.in[0] = desc(in);
+    lr.l0[0] = Y;
+    lr.l0_pitch[0] = y_pitch;
+    lr.l1[0] = Y1;
+    lr.l1_pitch[0] = y1_pitch;
+    lr.count = 1;
+    cudaError_t e = launch_luma_reduce(lr, static_cast<cudaStream_t>(cuda_stream));
+    return e == cudaSuccess ? PANO_OK : cuda_fail(e, "luma/REDUCE launch");
 }
 
 pano_status pano_stage_pyr_down(const float* src, int h, int w, int src_pitch, float* dst, int dst_pitch,

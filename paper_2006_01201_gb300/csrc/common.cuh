@@ -110,6 +110,17 @@ struct LumaArgs {
     int pyr;                        // PyrType of the output planes
 };
 
+// Level 0 (luma) and level 1 (its REDUCE) of up to kMaxPlanes images in one
+// launch.
+struct LumaReduceArgs {
+    ImageDesc in[kMaxPlanes];
+    void* l0[kMaxPlanes];           // planes of type pyr
+    void* l1[kMaxPlanes];
+    int l0_pitch[kMaxPlanes], l1_pitch[kMaxPlanes];  // elements
+    int count;
+    int pyr;
+};
+
 // One REDUCE step of up to kMaxPlanes planes of any sizes in one launch.
 struct PyrDownArgs {
     const void* src[kMaxPlanes];    // planes of type pyr
@@ -205,6 +216,7 @@ struct EnergyArgs {
 // Launchers: enqueue on `s`, return the launch error (cudaSuccess if none).
 cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s);
 cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s);
+cudaError_t launch_luma_reduce(const LumaReduceArgs& a, cudaStream_t s);
 // One LK level: streamed (lk_stream.cu) for levels of at least
 // kStreamMinPixels pixels and 1 <= iters <= 5, tiled (lk.cu) otherwise.
 // Levels below kSmallTilePixels use small tiles (kSmallTileW x kSmallTileH):

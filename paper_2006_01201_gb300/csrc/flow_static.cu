@@ -195,9 +195,26 @@ pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L
         }
     }
     cudaError_t e;
-    if (la.count > 0 && (e = launch_luma(la, s)) != cudaSuccess)
+    int first = 1;  // first level left to REDUCE
+    if (la.count == 2 && nlev >= 2) {
+        // level 0 and level 1 of both strips in one launch (as pano_flow_pair)
+        LumaReduceArgs lr;
+        memset(&lr, 0, sizeof(lr));
+        for (int i = 0; i < 2; ++i) {
+            lr.in[i] = la.in[i];
+            lr.l0[i] = la.out[i];
+            lr.l0_pitch[i] = la.out_pitch[i];
+            lr.l1[i] = pyr[i][1];
+            lr.l1_pitch[i] = lp[1];
+        }
+        lr.count = 2;
+        if ((e = launch_luma_reduce(lr, s)) != cudaSuccess)
+            return sfail(PANO_ERR_CUDA, "luma launch: %s", cudaGetErrorString(e));
+        first = 2;
+    } else if (la.count > 0 && (e = launch_luma(la, s)) != cudaSuccess) {
         return sfail(PANO_ERR_CUDA, "luma launch: %s", cudaGetErrorString(e));
-    for (int l = 1; l < nlev; ++l) {
+    }
+    for (int l = first; l < nlev; ++l) {
         PyrDownArgs pa;
         memset(&pa, 0, sizeof(pa));
         for (int si = 0; si < 2; ++si) {

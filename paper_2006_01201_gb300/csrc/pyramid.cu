@@ -24,17 +24,38 @@ constexpr float kInv255 = 1.0f / 255.0f;
 // mantissa bits, minus 2^23 (no integer-to-float conversion).
 __device__ __forceinline__ float byte_f(uint32_t b) { return __uint_as_float(0x4B000000u | b) - 8388608.0f; }
 
+// BT.601 luma with a fixed order of operations, shared by every kernel that
+// forms level 0 (so that all of them give the same bits).
+__device__ __forceinline__ float luma3(float r, float g, float b) { return fmaf(0.114f, b, fmaf(0.587f, g, 0.299f * r)); }
+
 __device__ __forceinline__ float luma_at(const ImageDesc& in, const unsigned char* row, int x) {
     if (in.dtype == 0) {
         if (in.c == 3) {
             const uint8_t* px = row + 3 * x;
-            return (0.299f * byte_f(px[0]) + 0.587f * byte_f(px[1]) + 0.114f * byte_f(px[2])) * kInv255;
+            return luma3(byte_f(px[0]), byte_f(px[1]), byte_f(px[2])) * kInv255;
         }
         return byte_f(row[x]) * kInv255;
     }
     const float* r = reinterpret_cast<const float*>(row);
-    if (in.c == 3) return 0.299f * r[3 * x] + 0.587f * r[3 * x + 1] + 0.114f * r[3 * x + 2];
+    if (in.c == 3) return luma3(r[3 * x], r[3 * x + 1], r[3 * x + 2]);
     return r[x];
+}
+
+// Luma of the four pixels x .. x+3 of a row (all inside the row): 12 aligned
+// bytes for u8 RGB when the address allows it, else one pixel at a time.
+__device__ __forceinline__ void luma4(const ImageDesc& in, const unsigned char* row, int x, float (&v)[4]) {
+    if (in.dtype == 0 && in.c == 3 && ((((uintptr_t)row) + 3 * x) & 3) == 0) {
+        const uint32_t* p = reinterpret_cast<const uint32_t*>(row + 3 * x);
+        const uint32_t w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2);
+        const uint32_t b[12] = {w0 & 255, (w0 >> 8) & 255, (w0 >> 16) & 255, w0 >> 24,
+                                w1 & 255, (w1 >> 8) & 255, (w1 >> 16) & 255, w1 >> 24,
+                                w2 & 255, (w2 >> 8) & 255, (w2 >> 16) & 255, w2 >> 24};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = luma3(byte_f(b[3 * k]), byte_f(b[3 * k + 1]), byte_f(b[3 * k + 2])) * kInv255;
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = luma_at(in, row, x + k);
 }
 
 // Four consecutive outputs: one 16-byte store for float32 rows, one 8-byte
@@ -70,17 +91,9 @@ __global__ void __launch_bounds__(256) luma_kernel(const __grid_constant__ LumaA
     if (x >= in.w || y >= in.h) return;
     const unsigned char* row = static_cast<const unsigned char*>(in.data) + (long long)y * in.pitch_bytes;
     To* orow = out + (long long)y * out_pitch;
-    if (x + 4 <= in.w && in.dtype == 0 && in.c == 3 && ((((uintptr_t)row) + 3 * x) & 3) == 0) {
-        // 12 aligned bytes = 4 RGB pixels
-        const uint32_t* p = reinterpret_cast<const uint32_t*>(row + 3 * x);
-        const uint32_t w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2);
+    if (x + 4 <= in.w) {
         float v[4];
-        const uint32_t b[12] = {w0 & 255, (w0 >> 8) & 255, (w0 >> 16) & 255, w0 >> 24,
-                                w1 & 255, (w1 >> 8) & 255, (w1 >> 16) & 255, w1 >> 24,
-                                w2 & 255, (w2 >> 8) & 255, (w2 >> 16) & 255, w2 >> 24};
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-            v[k] = (0.299f * byte_f(b[3 * k]) + 0.587f * byte_f(b[3 * k + 1]) + 0.114f * byte_f(b[3 * k + 2])) * kInv255;
+        luma4(in, row, x, v);
         store4(orow + x, v);
         return;
     }
@@ -97,6 +110,12 @@ __global__ void __launch_bounds__(256) luma_kernel(const __grid_constant__ LumaA
 // at the even columns.
 // ---------------------------------------------------------------------------
 constexpr int kPdTW = 64, kPdTH = 16;
+
+// One 5-tap binomial sum [1 4 6 4 1]/16 with a fixed order of operations.
+__device__ __forceinline__ float reduce5(float a, float b, float c, float d, float e) {
+    const float k0 = 1.0f / 16, k1 = 4.0f / 16, k2 = 6.0f / 16;
+    return fmaf(k0, e, fmaf(k1, d, fmaf(k2, c, fmaf(k1, b, k0 * a))));
+}
 constexpr int kPdSH = 2 * kPdTH + 3;  // source rows 2*y0-2 .. 2*(y0+15)+2
 constexpr int kPdQ = (2 * kPdTW + 8) / 4;  // groups of four source columns from 2*x0-4
 constexpr int kPdSW = 4 * kPdQ;            // staged columns 2*x0-4 .. 2*x0+131
@@ -121,6 +140,32 @@ __device__ __forceinline__ void widen4(const uint2& v, float* o) {
     const Ts* e = reinterpret_cast<const Ts*>(&v);
 #pragma unroll
     for (int k = 0; k < 4; ++k) o[k] = to_f32(e[k]);
+}
+
+// Blur the staged footprint along y at the even rows and along x at the even
+// columns, and store the 64 x 16 destination tile (one barrier inside).
+template <class Ts>
+__device__ __forceinline__ void reduce_staged(const float (*s_src)[kPdSW], float (*s_v)[kPdSW + 1], int xd0, int yd0,
+                                              int wd, int hd, Ts* __restrict__ dst, int dst_pitch) {
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kPdTH * kPdSW; i += 256) {
+        int r = i / kPdSW, c = i - r * kPdSW;
+        int sr = 2 * r + 2;
+        s_v[r][c] = reduce5(s_src[sr - 2][c], s_src[sr - 1][c], s_src[sr][c], s_src[sr + 1][c], s_src[sr + 2][c]);
+    }
+    __syncthreads();
+    const int x = tid & (kPdTW - 1);
+    const int xd = xd0 + x;
+    if (xd < wd) {
+        const int c = 2 * x + 4;  // staged column of source column 2 * xd
+#pragma unroll
+        for (int r = tid / kPdTW; r < kPdTH; r += 256 / kPdTW) {
+            const int yd = yd0 + r;
+            if (yd >= hd) break;
+            const float* v = s_v[r];
+            dst[(long long)yd * dst_pitch + xd] = from_f32<Ts>(reduce5(v[c - 2], v[c - 1], v[c], v[c + 1], v[c + 2]));
+        }
+    }
 }
 
 template <class Ts>
@@ -156,30 +201,81 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ P
         }
     }
     __syncthreads();
-    const float k0 = 1.0f / 16, k1 = 4.0f / 16, k2 = 6.0f / 16;
-    for (int i = tid; i < kPdTH * kPdSW; i += 256) {
-        int r = i / kPdSW, c = i - r * kPdSW;
-        int sr = 2 * r + 2;
-        s_v[r][c] = k0 * s_src[sr - 2][c] + k1 * s_src[sr - 1][c] + k2 * s_src[sr][c] +
-                    k1 * s_src[sr + 1][c] + k0 * s_src[sr + 2][c];
-    }
     __syncthreads();
-    const int x = tid & (kPdTW - 1);
-    const int xd = xd0 + x;
-    if (xd < wd) {
-        const int c = 2 * x + 4;  // staged column of source column 2 * xd
+    reduce_staged<Ts>(s_src, s_v, xd0, yd0, wd, hd, dst, dst_pitch);
+}
+
+// Level 0 and level 1 in one pass: a block computes the luma of the footprint
+// of its 64 x 16 level-1 tile (35 rows x 136 columns, clamped), rounded to
+// the storage type as level 0 is stored, writes the level-0 pixels it owns
+// (rows 2*y0 .. 2*y0+31, columns 2*x0 .. 2*x0+127; the blocks tile level 0
+// exactly) and reduces the footprint to the level-1 tile. Same values as
+// luma_kernel followed by pyr_down_kernel.
+template <class Ts>
+__global__ void __launch_bounds__(256) luma_reduce_kernel(const __grid_constant__ LumaReduceArgs a) {
+    __shared__ __align__(16) float s_src[kPdSH][kPdSW];
+    __shared__ float s_v[kPdTH][kPdSW + 1];
+    const int z = blockIdx.z;
+    const ImageDesc& in = a.in[z];
+    const int h = in.h, w = in.w;
+    const int hd = (h + 1) >> 1, wd = (w + 1) >> 1;
+    const int xd0 = blockIdx.x * kPdTW, yd0 = blockIdx.y * kPdTH;
+    if (xd0 >= wd || yd0 >= hd) return;  // a smaller plane of the batch
+    const int cx0 = 2 * xd0 - 4, sy0 = 2 * yd0 - 2;
+    Ts* __restrict__ l0 = static_cast<Ts*>(a.l0[z]);
+    const int p0 = a.l0_pitch[z];
+    const int tid = threadIdx.x;
+    for (int i = tid; i < kPdSH * kPdQ; i += 256) {
+        const int r = i / kPdQ, q = i - r * kPdQ;
+        const int yy = sy0 + r;
+        const int sy = min(max(yy, 0), h - 1);
+        const int sx = cx0 + 4 * q;
+        const unsigned char* row = static_cast<const unsigned char*>(in.data) + (long long)sy * in.pitch_bytes;
+        float v[4];
+        if (sx >= 0 && sx + 3 < w) {
+            luma4(in, row, sx, v);
+        } else {
 #pragma unroll
-        for (int r = tid / kPdTW; r < kPdTH; r += 256 / kPdTW) {
-            const int yd = yd0 + r;
-            if (yd >= hd) break;
-            const float* v = s_v[r];
-            dst[(long long)yd * dst_pitch + xd] =
-                from_f32<Ts>(k0 * v[c - 2] + k1 * v[c - 1] + k2 * v[c] + k1 * v[c + 1] + k0 * v[c + 2]);
+            for (int k = 0; k < 4; ++k) v[k] = luma_at(in, row, min(max(sx + k, 0), w - 1));
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = to_f32(from_f32<Ts>(v[k]));  // the stored level-0 value
+        float* o = &s_src[r][4 * q];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) o[k] = v[k];
+        // level-0 pixels owned by this block
+        if (r >= 2 && r < 2 + 2 * kPdTH && yy < h && q >= 1 && q <= kPdTW / 2 && sx < w) {
+            Ts* orow = l0 + (long long)yy * p0;
+            if (sx + 3 < w) {
+                store4(orow + sx, v);
+            } else {
+                for (int k = 0; k < 4 && sx + k < w; ++k) orow[sx + k] = from_f32<Ts>(v[k]);
+            }
         }
     }
+    __syncthreads();
+    reduce_staged<Ts>(s_src, s_v, xd0, yd0, wd, hd, static_cast<Ts*>(a.l1[z]), a.l1_pitch[z]);
 }
 
 }  // namespace
+
+cudaError_t launch_luma_reduce(const LumaReduceArgs& a, cudaStream_t s) {
+    if (a.count < 1 || a.count > kMaxPlanes) return cudaErrorInvalidValue;
+    int hd = 0, wd = 0;
+    for (int i = 0; i < a.count; ++i) {
+        hd = max(hd, (a.in[i].h + 1) / 2);
+        wd = max(wd, (a.in[i].w + 1) / 2);
+    }
+    dim3 block(256);
+    dim3 grid((wd + kPdTW - 1) / kPdTW, (hd + kPdTH - 1) / kPdTH, a.count);
+    switch (a.pyr) {
+        case kPyrF32: luma_reduce_kernel<float><<<grid, block, 0, s>>>(a); break;
+        case kPyrBF16: luma_reduce_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(a); break;
+        case kPyrF16: luma_reduce_kernel<__half><<<grid, block, 0, s>>>(a); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s) {
     if (a.count < 1 || a.count > kMaxPlanes) return cudaErrorInvalidValue;

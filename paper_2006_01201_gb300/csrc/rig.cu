@@ -277,14 +277,35 @@ cudaError_t enqueue_all(pano_rig* r, const RunCall& c, cudaStream_t s, bool trac
             la.count++;
         }
     la.pyr = pyr_type(r->p.pyr_dtype);
-    if (la.count) {
+    int first = 1;  // first level left to REDUCE
+    if (la.count == 2 * n && r->nlev >= 2) {
+        // level 0 and level 1 of every strip in one launch (as pano_flow_pair)
+        LumaReduceArgs lr;
+        memset(&lr, 0, sizeof(lr));
+        int i = 0;
+        for (int k = 0; k < n; ++k)
+            for (int si = 0; si < 2; ++si, ++i) {
+                lr.in[i] = la.in[i];
+                lr.l0[i] = la.out[i];
+                lr.l0_pitch[i] = la.out_pitch[i];
+                lr.l1[i] = r->pyr[k][si][1];
+                lr.l1_pitch[i] = r->lev_pitch[k][1];
+            }
+        lr.count = la.count;
+        lr.pyr = la.pyr;
+        int slot = trace ? trace_begin(r->tr, PANO_TRACE_LUMA_REDUCE, 1, s) : -1;
+        if ((e = launch_luma_reduce(lr, s)) != cudaSuccess) return e;
+        if (slot >= 0) trace_end(r->tr, slot, s);
+        ++*kernels;
+        first = 2;
+    } else if (la.count) {
         int slot = trace ? trace_begin(r->tr, PANO_TRACE_LUMA, 0, s) : -1;
         if ((e = launch_luma(la, s)) != cudaSuccess) return e;
         if (slot >= 0) trace_end(r->tr, slot, s);
         ++*kernels;
     }
     // REDUCE of every strip, one launch per level
-    for (int l = 1; l < r->nlev; ++l) {
+    for (int l = first; l < r->nlev; ++l) {
         PyrDownArgs pa;
         memset(&pa, 0, sizeof(pa));
         for (int k = 0; k < n; ++k)

@@ -77,6 +77,23 @@ def test_pyr_down_matches_oracle(shape):
     np.testing.assert_allclose(out, oracle.pyr_down(src), rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("shape,dtype", [((37, 53, 3), np.uint8), ((64, 96, 1), np.uint8), ((130, 260, 3), np.uint8),
+                                         ((35, 131, 3), np.float32), ((1, 1, 3), np.uint8), ((2, 300, 1), np.float32)])
+def test_fused_luma_and_reduce_equal_the_separate_kernels_and_the_oracle(shape, dtype):
+    g = rng(31)
+    img = g.integers(0, 256, size=shape).astype(np.uint8) if dtype == np.uint8 else \
+        g.uniform(0, 1, size=shape).astype(np.float32)
+    t = cuda(img if shape[2] == 3 else img[..., 0])
+    Y, Y1 = binding.stage_luma_pyr(t)
+    Ys = binding.stage_luma(t)
+    Y1s = binding.stage_pyr_down(Ys)
+    torch.cuda.synchronize()
+    assert torch.equal(Y, Ys) and torch.equal(Y1, Y1s)
+    Yo = oracle.luma(oracle.to_unit(img if shape[2] == 3 else img[..., 0]))
+    np.testing.assert_allclose(host(Y), Yo, rtol=0, atol=1e-6)
+    np.testing.assert_allclose(host(Y1), oracle.pyr_down(Yo), rtol=0, atol=1e-6)
+
+
 def test_pyr_down_respects_row_pitch():
     big = rng(3).uniform(0, 1, size=(40, 64)).astype(np.float32)
     view = cuda(big)[:, :45]                      # rows of 64 elements, 45 used
