@@ -415,14 +415,14 @@ def run_gpu(args):
     value = throughput(h * w, args.steps, world, total_ms)
 
     # --- same loop with every launch bracketed by events: per-kernel times
-    ctx.trace_enable(0x1F, 64 * args.steps)
+    ctx.trace_enable(0x3F, 64 * args.steps)
     for k in range(args.steps):
         flush.zero_()
         step()
     torch.cuda.synchronize()
     recs = ctx.trace_read(64 * args.steps)
     ctx.trace_enable(0, 0)
-    names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "blend_kernel", 16: "luma_reduce_kernel"}
+    names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "blend_kernel", 16: "luma_reduce_kernel", 32: "pyr_tail_kernel"}
     npx = level_pixels(h, w, levels)
     lk_bytes = lk_alg_bytes(h, w, levels, elem)
     per_kind = {}
@@ -744,7 +744,7 @@ def run_rig(args):
     value = throughput(npx, args.steps, world, total_ms)
 
     # --- eager runs with every launch bracketed by events: per-kernel times
-    rig.trace_enable(0x1F, 64 * args.steps)
+    rig.trace_enable(0x3F, 64 * args.steps)
     for k in range(args.steps):
         flush.zero_()
         rig.run(Ls, Rs, canvas=canvas, use_graph=False, stream=stream)
@@ -753,7 +753,7 @@ def run_rig(args):
     rig.trace_enable(0, 0)
     plan = rig_level_kernels(h, widths, levels, [t["kernel"] for t in tunings],
                              [(t["tile_w"], t["tile_h"]) for t in tunings])
-    names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "rig_blend_kernel", 16: "luma_reduce_kernel"}
+    names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "rig_blend_kernel", 16: "luma_reduce_kernel", 32: "pyr_tail_kernel"}
     per_kind, lk_seen = {}, {}
     stream_bytes = 0.0
     lk_bytes = [lk_alg_bytes(h, w, levels, elem) for w in widths]

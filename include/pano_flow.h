@@ -248,6 +248,7 @@ PANO_API pano_status pano_flow_pair_static(const pano_flow_params* params, const
 #define PANO_TRACE_LK       0x4u   /* one Lucas-Kanade level, both directions */
 #define PANO_TRACE_BLEND    0x8u   /* Code 1 blend */
 #define PANO_TRACE_LUMA_REDUCE 0x10u  /* level 0 (luma) and level 1 (its REDUCE) in one launch */
+#define PANO_TRACE_PYR_TAIL 0x20u  /* several REDUCE steps (levels 3 and below) in one launch */
 
 typedef struct pano_trace_record {
     int kind;     /* one PANO_TRACE_* bit */
@@ -286,6 +287,15 @@ PANO_API pano_status pano_stage_luma(const pano_image* in, float* Y, int y_pitch
  * Pitches in floats. */
 PANO_API pano_status pano_stage_luma_pyr(const pano_image* in, float* Y, int y_pitch, float* Y1, int y1_pitch,
                                          void* cuda_stream);
+
+/* Levels 1 .. nlev-1 of the pyramid of Y (h x w, row pitch `pitch` floats)
+ * with the launch sequence pano_flow_pair uses (one-level REDUCE launches
+ * for levels 1 and 2, several levels per launch after that): levels[l - 1]
+ * receives level l, ceil(h / 2^l) x ceil(w / 2^l), row pitch pitches[l - 1]
+ * floats. The same values as nlev - 1 pano_stage_pyr_down calls, bit for
+ * bit. nlev in 2..12. */
+PANO_API pano_status pano_stage_pyramid(const float* Y, int h, int w, int pitch, float* const* levels,
+                                        const int* pitches, int nlev, void* cuda_stream);
 
 /* One pyramid REDUCE step (Section III-C-1, "LK pyramid"): [1 4 6 4 1]/16
  * along y then x, replicate border, keep even rows and columns.

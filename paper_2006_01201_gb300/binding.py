@@ -70,6 +70,7 @@ _PP = ctypes.POINTER(ctypes.c_void_p)
 
 PANO_TRACE_LUMA, PANO_TRACE_PYR_DOWN, PANO_TRACE_LK, PANO_TRACE_BLEND = 0x1, 0x2, 0x4, 0x8
 PANO_TRACE_LUMA_REDUCE = 0x10
+PANO_TRACE_PYR_TAIL = 0x20
 
 SIGNATURES = {
     "pano_flow_params_default": ([_PAR], None),
@@ -87,6 +88,7 @@ SIGNATURES = {
     "pano_stage_luma": ([_IMG, _VP, _I, _VP], _I),
     "pano_stage_pyr_down": ([_VP, _I, _I, _I, _VP, _I, _VP], _I),
     "pano_stage_luma_pyr": ([_IMG, _VP, _I, _VP, _I, _VP], _I),
+    "pano_stage_pyramid": ([_VP, _I, _I, _I, _PP, ctypes.POINTER(ctypes.c_int), _I, _VP], _I),
     "pano_stage_lk": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _VP], _I),
     "pano_stage_warp": ([_IMG, _VP, _F, _IMG, _VP], _I),
     "pano_blend_coeff_scratch_bytes": ([_I, _I], ctypes.c_size_t),
@@ -640,6 +642,25 @@ def stage_luma_pyr(img, stream=None):
     _check(load_library().pano_stage_luma_pyr(ctypes.byref(d), Y.data_ptr(), d.w, Y1.data_ptr(), Y1.shape[1],
                                               _stream_ptr(stream)))
     return Y, Y1
+
+
+def stage_pyramid(Y, nlev: int, stream=None):
+    """[level 1, ..., level nlev-1] of a float32 (H, W) CUDA tensor, with the
+    launch sequence of the flow path."""
+    torch = _torch()
+    if Y.dtype != torch.float32 or Y.dim() != 2 or Y.stride(1) != 1:
+        raise PanoError(PANO_ERR_INVALID_ARG, "Y must be a float32 (H, W) tensor with contiguous rows")
+    h, w = Y.shape
+    outs = []
+    for _ in range(nlev - 1):
+        h, w = (h + 1) // 2, (w + 1) // 2
+        outs.append(torch.empty((h, w), dtype=torch.float32, device=Y.device))
+    ptrs = (ctypes.c_void_p * len(outs))(*[o.data_ptr() for o in outs])
+    pitches = (ctypes.c_int * len(outs))(*[o.shape[1] for o in outs])
+    pitch = Y.stride(0) if Y.shape[0] > 1 else Y.shape[1]
+    _check(load_library().pano_stage_pyramid(Y.data_ptr(), Y.shape[0], Y.shape[1], pitch, ptrs, pitches, nlev,
+                                             _stream_ptr(stream)))
+    return outs
 
 
 def stage_pyr_down(src, stream=None):

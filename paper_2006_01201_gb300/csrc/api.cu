@@ -129,6 +129,7 @@ pano_status ensure_lk_ready(int* max_smem_out) {
     if (dev >= 0 && dev < 64 && !prepared[dev]) {
         if ((e = lk_prepare(ms)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         if ((e = blend_coeff_prepare(ms)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        if ((e = pyr_tail_prepare(ms)) != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
         prepared[dev] = 1;
     }
     *max_smem_out = ms;
@@ -263,6 +264,62 @@ void pair_planes(const pano_flow_ctx* c, const pano_image* L, const pano_image* 
     pp->luma.pyr = pyr_type(c->p.pyr_dtype);
 }
 
+cudaError_t launch_pyramid_rest(const PyrSet& ps, int first, Trace* tr, cudaStream_t s, int* kernels) {
+    auto size = [&](int i, int l, int* h, int* w) {
+        *h = ps.h0[i];
+        *w = ps.w0[i];
+        for (int k = 0; k < l; ++k) {
+            *h = (*h + 1) / 2;
+            *w = (*w + 1) / 2;
+        }
+    };
+    cudaError_t e;
+    int l = first;
+    while (l < ps.nlev) {
+        const int m = ps.nlev - l < kTailMaxLevels ? ps.nlev - l : kTailMaxLevels;
+        if (l >= 3 && m >= 2) {
+            // levels l .. l+m-1 from level l-1 in one launch
+            PyrTailArgs ta;
+            memset(&ta, 0, sizeof(ta));
+            for (int i = 0; i < ps.count; ++i) {
+                ta.src[i] = ps.plane[i][l - 1];
+                ta.src_pitch[i] = ps.pitch[i][l - 1];
+                size(i, l - 1, &ta.h[i], &ta.w[i]);
+                for (int j = 0; j < m; ++j) {
+                    ta.dst[i][j] = const_cast<void*>(ps.plane[i][l + j]);
+                    ta.dst_pitch[i][j] = ps.pitch[i][l + j];
+                }
+            }
+            ta.count = ps.count;
+            ta.levels = m;
+            ta.pyr = ps.pyr;
+            const int t = tr ? trace_begin(*tr, PANO_TRACE_PYR_TAIL, l, s) : -1;
+            if ((e = launch_pyr_tail(ta, s)) != cudaSuccess) return e;
+            if (tr) trace_end(*tr, t, s);
+            ++*kernels;
+            l += m;
+            continue;
+        }
+        PyrDownArgs pa;
+        memset(&pa, 0, sizeof(pa));
+        for (int i = 0; i < ps.count; ++i) {
+            pa.src[i] = ps.plane[i][l - 1];
+            pa.src_pitch[i] = ps.pitch[i][l - 1];
+            pa.dst[i] = const_cast<void*>(ps.plane[i][l]);
+            pa.dst_pitch[i] = ps.pitch[i][l];
+            size(i, l - 1, &pa.h[i], &pa.w[i]);
+        }
+        pa.count = ps.count;
+        pa.pyr = ps.pyr;
+        const int t = tr ? trace_begin(*tr, PANO_TRACE_PYR_DOWN, l, s) : -1;
+        if ((e = launch_pyr_down(pa, s)) != cudaSuccess) return e;
+        if (tr) trace_end(*tr, t, s);
+        ++*kernels;
+        ++l;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_pair_pyramid(pano_flow_ctx* c, const PairPlanes& pp, cudaStream_t s) {
     cudaError_t e;
     int first = 1;  // first level left to REDUCE
@@ -290,25 +347,23 @@ cudaError_t launch_pair_pyramid(pano_flow_ctx* c, const PairPlanes& pp, cudaStre
         trace_end(c->tr, t, s);
         c->launches++;
     }
-    for (int l = first; l < c->nlev; ++l) {
-        PyrDownArgs pa;
-        memset(&pa, 0, sizeof(pa));
-        for (int si = 0; si < 2; ++si) {
-            pa.src[si] = pp.plane[si][l - 1];
-            pa.src_pitch[si] = pp.pitch[si][l - 1];
-            pa.dst[si] = c->pyr[si][l];
-            pa.dst_pitch[si] = c->lev_pitch[l];
+    PyrSet ps;
+    memset(&ps, 0, sizeof(ps));
+    for (int si = 0; si < 2; ++si) {
+        for (int l = 0; l < c->nlev; ++l) {
+            ps.plane[si][l] = pp.plane[si][l];
+            ps.pitch[si][l] = pp.pitch[si][l];
         }
-        pa.h[0] = pa.h[1] = pp.hs[l - 1];
-        pa.w[0] = pa.w[1] = pp.ws[l - 1];
-        pa.count = 2;
-        pa.pyr = pyr_type(c->p.pyr_dtype);
-        int t = trace_begin(c->tr, PANO_TRACE_PYR_DOWN, l, s);
-        if ((e = launch_pyr_down(pa, s)) != cudaSuccess) return e;
-        trace_end(c->tr, t, s);
-        c->launches++;
+        ps.h0[si] = pp.hs[0];
+        ps.w0[si] = pp.ws[0];
     }
-    return cudaSuccess;
+    ps.count = 2;
+    ps.nlev = c->nlev;
+    ps.pyr = pyr_type(c->p.pyr_dtype);
+    int kernels = 0;
+    e = launch_pyramid_rest(ps, first, &c->tr, s, &kernels);
+    c->launches += kernels;
+    return e;
 }
 
 void pair_lk_args(const pano_flow_ctx* c, const PairPlanes& pp, int l, float* flow_LtoR, float* flow_RtoL,
@@ -532,6 +587,38 @@ pano_status pano_stage_luma_pyr(const pano_image* in, float* Y, int y_pitch, flo
     lr.count = 1;
     cudaError_t e = launch_luma_reduce(lr, static_cast<cudaStream_t>(cuda_stream));
     return e == cudaSuccess ? PANO_OK : cuda_fail(e, "luma/REDUCE launch");
+}
+
+pano_status pano_stage_pyramid(const float* Y, int h, int w, int pitch, float* const* levels, const int* pitches,
+                               int nlev, void* cuda_stream) {
+    if (!Y || ((uintptr_t)Y) % 4) return fail(PANO_ERR_INVALID_ARG, "Y is NULL or misaligned");
+    if (h < 1 || w < 1 || pitch < w) return fail(PANO_ERR_INVALID_ARG, "bad size or pitch");
+    if (nlev < 2 || nlev > kMaxLevels) return fail(PANO_ERR_INVALID_ARG, "nlev %d not in 2..%d", nlev, kMaxLevels);
+    if (!levels || !pitches) return fail(PANO_ERR_INVALID_ARG, "levels or pitches is NULL");
+    PyrSet ps;
+    memset(&ps, 0, sizeof(ps));
+    ps.plane[0][0] = Y;
+    ps.pitch[0][0] = pitch;
+    int lh = h, lw = w;
+    for (int l = 1; l < nlev; ++l) {
+        lh = (lh + 1) / 2;
+        lw = (lw + 1) / 2;
+        if (!levels[l - 1] || ((uintptr_t)levels[l - 1]) % 4)
+            return fail(PANO_ERR_INVALID_ARG, "level %d is NULL or misaligned", l);
+        if (pitches[l - 1] < lw) return fail(PANO_ERR_INVALID_ARG, "pitch of level %d < %d", l, lw);
+        ps.plane[0][l] = levels[l - 1];
+        ps.pitch[0][l] = pitches[l - 1];
+    }
+    ps.h0[0] = h;
+    ps.w0[0] = w;
+    ps.count = 1;
+    ps.nlev = nlev;
+    int st_ms = 0;
+    pano_status st;
+    if ((st = ensure_lk_ready(&st_ms)) != PANO_OK) return st;
+    int kernels = 0;
+    cudaError_t e = launch_pyramid_rest(ps, 1, nullptr, static_cast<cudaStream_t>(cuda_stream), &kernels);
+    return e == cudaSuccess ? PANO_OK : cuda_fail(e, "pyramid launch");
 }
 
 pano_status pano_stage_pyr_down(const float* src, int h, int w, int src_pitch, float* dst, int dst_pitch,

@@ -121,6 +121,18 @@ struct LumaReduceArgs {
     int pyr;
 };
 
+// Several REDUCE steps of up to kMaxPlanes planes in one launch: levels
+// s+1 .. s+levels from level s (pyramid.cu, pyr_tail_kernel).
+constexpr int kTailMaxLevels = 4;
+struct PyrTailArgs {
+    const void* src[kMaxPlanes];    // level s, planes of type pyr
+    int src_pitch[kMaxPlanes];
+    int h[kMaxPlanes], w[kMaxPlanes];  // size of level s
+    void* dst[kMaxPlanes][kTailMaxLevels];  // levels s+1 .. s+levels
+    int dst_pitch[kMaxPlanes][kTailMaxLevels];
+    int count, levels, pyr;
+};
+
 // One REDUCE step of up to kMaxPlanes planes of any sizes in one launch.
 struct PyrDownArgs {
     const void* src[kMaxPlanes];    // planes of type pyr
@@ -217,6 +229,8 @@ struct EnergyArgs {
 cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s);
 cudaError_t launch_pyr_down(const PyrDownArgs& a, cudaStream_t s);
 cudaError_t launch_luma_reduce(const LumaReduceArgs& a, cudaStream_t s);
+cudaError_t launch_pyr_tail(const PyrTailArgs& a, cudaStream_t s);
+cudaError_t pyr_tail_prepare(int max_smem_bytes);
 // One LK level: streamed (lk_stream.cu) for levels of at least
 // kStreamMinPixels pixels and 1 <= iters <= 5, tiled (lk.cu) otherwise.
 // Levels below kSmallTilePixels use small tiles (kSmallTileW x kSmallTileH):

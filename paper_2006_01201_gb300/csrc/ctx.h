@@ -73,6 +73,19 @@ bool pick_tile(int iters, int radius, int max_smem, int* tw, int* th);
 // sets the kernels' shared-memory limits once per device; returns the limit
 pano_status ensure_lk_ready(int* max_smem_out);
 
+// The pyramid levels below level 1 (or 0): one REDUCE launch per level for
+// levels 1 and 2, then launches of up to four levels each. plane/pitch give
+// every level of every plane (level 0 of a plane may be the strip itself);
+// h0/w0 the level-0 sizes. Launches are traced in *tr (if not null) and
+// added to *kernels.
+struct PyrSet {
+    const void* plane[kMaxPlanes][kMaxLevels];
+    int pitch[kMaxPlanes][kMaxLevels];
+    int h0[kMaxPlanes], w0[kMaxPlanes];
+    int count, nlev, pyr;
+};
+cudaError_t launch_pyramid_rest(const PyrSet& ps, int first, Trace* tr, cudaStream_t s, int* kernels);
+
 void trace_free(Trace& t);
 pano_status trace_enable(Trace& t, unsigned kind_mask, int capacity);
 pano_status trace_read(Trace& t, pano_trace_record* out, int max_records, int* n_out);

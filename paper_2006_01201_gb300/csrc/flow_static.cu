@@ -20,6 +20,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "ctx.h"
 #include "pano_flow.h"
 
 using namespace pano;
@@ -76,8 +77,6 @@ pano_status setup_current_device(DeviceSetup** out) {
     *out = &s;
     return PANO_OK;
 }
-
-size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 pano_status check_img(const pano_image* im, const char* name) {
     if (!im || !im->data) return sfail(PANO_ERR_INVALID_ARG, "%s is NULL", name);
@@ -214,19 +213,22 @@ pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L
     } else if (la.count > 0 && (e = launch_luma(la, s)) != cudaSuccess) {
         return sfail(PANO_ERR_CUDA, "luma launch: %s", cudaGetErrorString(e));
     }
-    for (int l = first; l < nlev; ++l) {
-        PyrDownArgs pa;
-        memset(&pa, 0, sizeof(pa));
+    {
+        // the other levels (the same launch sequence as pano_flow_pair)
+        PyrSet ps;
+        memset(&ps, 0, sizeof(ps));
         for (int si = 0; si < 2; ++si) {
-            pa.src[si] = plane[si][l - 1];
-            pa.src_pitch[si] = ppitch[si][l - 1];
-            pa.dst[si] = pyr[si][l];
-            pa.dst_pitch[si] = lp[l];
+            for (int l = 0; l < nlev; ++l) {
+                ps.plane[si][l] = l == 0 ? (const void*)plane[si][0] : (const void*)pyr[si][l];
+                ps.pitch[si][l] = l == 0 ? ppitch[si][0] : lp[l];
+            }
+            ps.h0[si] = hs[0];
+            ps.w0[si] = ws[0];
         }
-        pa.h[0] = pa.h[1] = hs[l - 1];
-        pa.w[0] = pa.w[1] = ws[l - 1];
-        pa.count = 2;
-        if ((e = launch_pyr_down(pa, s)) != cudaSuccess)
+        ps.count = 2;
+        ps.nlev = nlev;
+        int kernels = 0;
+        if ((e = launch_pyramid_rest(ps, first, nullptr, s, &kernels)) != cudaSuccess)
             return sfail(PANO_ERR_CUDA, "pyramid launch: %s", cudaGetErrorString(e));
     }
     float* out[2] = {flow_LtoR, flow_RtoL};

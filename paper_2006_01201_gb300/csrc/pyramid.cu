@@ -257,7 +257,170 @@ __global__ void __launch_bounds__(256) luma_reduce_kernel(const __grid_constant_
     reduce_staged<Ts>(s_src, s_v, xd0, yd0, wd, hd, static_cast<Ts*>(a.l1[z]), a.l1_pitch[z]);
 }
 
+// ---------------------------------------------------------------------------
+// Levels s+1 .. s+M in one launch. A block owns a kTailTC x kTailTC tile of
+// the coarsest level and, at distance d from it, the 2^d-times larger tile;
+// the blocks tile every level exactly once. It stages the footprint of
+// level s that its tile needs (clamped), then forms each coarser level on
+// the region the next one needs: in-range pixels by the same two 5-tap
+// passes as pyr_down_kernel (each value rounded to the storage type, as it
+// is stored), pixels outside the level by copying the clamped in-range
+// pixel (the replicate border), and writes the pixels it owns. Same values
+// as M launches of pyr_down_kernel.
+// ---------------------------------------------------------------------------
+constexpr int kTailTC = 4;
+// side of the region needed at distance d: n(0) = TC, n(d) = 2 n(d-1) + 3
+__host__ __device__ constexpr int tail_n(int d) { return (kTailTC + 3) * (1 << d) - 3; }
+// offset of the buffer of distance d (the buffers of distances 0 .. d-1 before it)
+__host__ __device__ constexpr int tail_off(int d) {
+    int o = 0;
+    for (int e = 0; e < d; ++e) o += tail_n(e) * tail_n(e);
+    return o;
+}
+// the vertical-pass buffer: the largest n(d) x n(d+1), d < m
+__host__ __device__ constexpr int tail_tmp(int m) {
+    int t = 0;
+    for (int d = 0; d < m; ++d) t = tail_n(d) * tail_n(d + 1) > t ? tail_n(d) * tail_n(d + 1) : t;
+    return t;
+}
+template <int M>
+struct TailSmem {
+    static constexpr int floats = tail_off(M + 1) + tail_tmp(M);
+    static constexpr size_t bytes = sizeof(float) * floats;
+};
+
+template <class Ts, int M>
+__global__ void __launch_bounds__(256) pyr_tail_kernel(const __grid_constant__ PyrTailArgs a) {
+    extern __shared__ float tsm[];
+    const int z = blockIdx.z;
+    // level sizes at distance d from the coarsest (ceil of repeated halving
+    // is the ceil of one division), and the first row / column of the
+    // region a block needs there: 2^d Yc - 2 (2^d - 1)
+    const int hs = a.h[z], ws = a.w[z];
+    auto H = [&](int d) { return (hs + (1 << (M - d)) - 1) >> (M - d); };
+    auto W = [&](int d) { return (ws + (1 << (M - d)) - 1) >> (M - d); };
+    const int Yc = blockIdx.y * kTailTC, Xc = blockIdx.x * kTailTC;
+    if (Yc >= H(0) || Xc >= W(0)) return;  // a smaller plane of the batch
+    auto Oy = [&](int d) { return (Yc << d) - 2 * ((1 << d) - 1); };
+    auto Ox = [&](int d) { return (Xc << d) - 2 * ((1 << d) - 1); };
+    const int tid = threadIdx.x;
+    float* tmp = tsm + tail_off(M + 1);
+    {
+        // footprint of level s, clamped
+        const Ts* __restrict__ src = static_cast<const Ts*>(a.src[z]);
+        const int pitch = a.src_pitch[z];
+        constexpr int n = tail_n(M);
+        float* b = tsm + tail_off(M);
+        for (int i = tid; i < n * n; i += 256) {
+            const int r = i / n, c = i - r * n;
+            const int y = min(max(Oy(M) + r, 0), H(M) - 1), x = min(max(Ox(M) + c, 0), W(M) - 1);
+            b[i] = ld_f32(src + (long long)y * pitch + x);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int d = M - 1; d >= 0; --d) {
+        const int nf = tail_n(d + 1), nc = tail_n(d);
+        const float* f = tsm + tail_off(d + 1);
+        float* c = tsm + tail_off(d);
+        // along y at the even rows of the finer level
+        for (int i = tid; i < nc * nf; i += 256) {
+            const int r = i / nf, q = i - r * nf;
+            const float* col = f + 2 * r * nf + q;
+            tmp[i] = reduce5(col[0], col[nf], col[2 * nf], col[3 * nf], col[4 * nf]);
+        }
+        __syncthreads();
+        // along x at the even columns, for the pixels inside the level
+        for (int i = tid; i < nc * nc; i += 256) {
+            const int r = i / nc, q = i - r * nc;
+            const int y = Oy(d) + r, x = Ox(d) + q;
+            if (y < 0 || y >= H(d) || x < 0 || x >= W(d)) continue;
+            const float* v = tmp + r * nf + 2 * q;
+            c[i] = to_f32(from_f32<Ts>(reduce5(v[0], v[1], v[2], v[3], v[4])));
+        }
+        __syncthreads();
+        // the replicate border: pixels outside the level take the clamped pixel
+        for (int i = tid; i < nc * nc; i += 256) {
+            const int r = i / nc, q = i - r * nc;
+            const int y = Oy(d) + r, x = Ox(d) + q;
+            if (y >= 0 && y < H(d) && x >= 0 && x < W(d)) continue;
+            const int cy = min(max(y, 0), H(d) - 1), cx = min(max(x, 0), W(d) - 1);
+            c[i] = c[(cy - Oy(d)) * nc + (cx - Ox(d))];
+        }
+        // the owned pixels of this level
+        Ts* __restrict__ dst = static_cast<Ts*>(a.dst[z][M - 1 - d]);
+        const int dp = a.dst_pitch[z][M - 1 - d];
+        const int t = kTailTC << d;
+        const int y0 = Yc << d, x0 = Xc << d;
+        for (int i = tid; i < t * t; i += 256) {
+            const int r = i / t, q = i - r * t;
+            const int y = y0 + r, x = x0 + q;
+            if (y >= H(d) || x >= W(d)) continue;
+            dst[(long long)y * dp + x] = from_f32<Ts>(c[(y - Oy(d)) * nc + (x - Ox(d))]);
+        }
+        __syncthreads();
+    }
+}
+
+template <class Ts, int M>
+cudaError_t launch_tail_m(const PyrTailArgs& a, cudaStream_t s) {
+    int hc = 0, wc = 0;
+    for (int i = 0; i < a.count; ++i) {
+        int h = a.h[i], w = a.w[i];
+        for (int d = 0; d < M; ++d) {
+            h = (h + 1) / 2;
+            w = (w + 1) / 2;
+        }
+        hc = max(hc, h);
+        wc = max(wc, w);
+    }
+    dim3 grid((wc + kTailTC - 1) / kTailTC, (hc + kTailTC - 1) / kTailTC, a.count);
+    pyr_tail_kernel<Ts, M><<<grid, 256, TailSmem<M>::bytes, s>>>(a);
+    return cudaGetLastError();
+}
+
+template <class Ts>
+cudaError_t launch_tail_t(const PyrTailArgs& a, cudaStream_t s) {
+    switch (a.levels) {
+        case 1: return launch_tail_m<Ts, 1>(a, s);
+        case 2: return launch_tail_m<Ts, 2>(a, s);
+        case 3: return launch_tail_m<Ts, 3>(a, s);
+        case 4: return launch_tail_m<Ts, 4>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class Ts>
+cudaError_t prepare_tail_t(int max_smem) {
+    const void* fns[] = {(const void*)pyr_tail_kernel<Ts, 1>, (const void*)pyr_tail_kernel<Ts, 2>,
+                         (const void*)pyr_tail_kernel<Ts, 3>, (const void*)pyr_tail_kernel<Ts, 4>};
+    const size_t need[] = {TailSmem<1>::bytes, TailSmem<2>::bytes, TailSmem<3>::bytes, TailSmem<4>::bytes};
+    for (int i = 0; i < 4; ++i) {
+        if (need[i] > (size_t)max_smem) return cudaErrorInvalidValue;
+        cudaError_t e = cudaFuncSetAttribute(fns[i], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need[i]);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 }  // namespace
+
+cudaError_t launch_pyr_tail(const PyrTailArgs& a, cudaStream_t s) {
+    if (a.count < 1 || a.count > kMaxPlanes || a.levels < 1 || a.levels > kTailMaxLevels) return cudaErrorInvalidValue;
+    switch (a.pyr) {
+        case kPyrF32: return launch_tail_t<float>(a, s);
+        case kPyrBF16: return launch_tail_t<__nv_bfloat16>(a, s);
+        case kPyrF16: return launch_tail_t<__half>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t pyr_tail_prepare(int max_smem_bytes) {
+    cudaError_t e;
+    if ((e = prepare_tail_t<float>(max_smem_bytes)) != cudaSuccess) return e;
+    if ((e = prepare_tail_t<__nv_bfloat16>(max_smem_bytes)) != cudaSuccess) return e;
+    return prepare_tail_t<__half>(max_smem_bytes);
+}
 
 cudaError_t launch_luma_reduce(const LumaReduceArgs& a, cudaStream_t s) {
     if (a.count < 1 || a.count > kMaxPlanes) return cudaErrorInvalidValue;

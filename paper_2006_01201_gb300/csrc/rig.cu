@@ -304,28 +304,24 @@ cudaError_t enqueue_all(pano_rig* r, const RunCall& c, cudaStream_t s, bool trac
         if (slot >= 0) trace_end(r->tr, slot, s);
         ++*kernels;
     }
-    // REDUCE of every strip, one launch per level
-    for (int l = first; l < r->nlev; ++l) {
-        PyrDownArgs pa;
-        memset(&pa, 0, sizeof(pa));
-        for (int k = 0; k < n; ++k)
-            for (int si = 0; si < 2; ++si) {
-                int sp = r->lev_pitch[k][l - 1];
-                const void* src = l == 1 ? level0(r, c, k, si, &sp) : r->pyr[k][si][l - 1];
-                pa.src[pa.count] = src;
-                pa.src_pitch[pa.count] = sp;
-                pa.dst[pa.count] = r->pyr[k][si][l];
-                pa.dst_pitch[pa.count] = r->lev_pitch[k][l];
-                pa.h[pa.count] = r->hs[l - 1];
-                pa.w[pa.count] = r->ws[k][l - 1];
-                pa.count++;
+    // the other levels of every strip (the same launch sequence as pano_flow_pair)
+    PyrSet ps;
+    memset(&ps, 0, sizeof(ps));
+    for (int k = 0; k < n; ++k)
+        for (int si = 0; si < 2; ++si) {
+            const int i = 2 * k + si;
+            for (int l = 0; l < r->nlev; ++l) {
+                int sp = r->lev_pitch[k][l];
+                ps.plane[i][l] = l == 0 ? level0(r, c, k, si, &sp) : r->pyr[k][si][l];
+                ps.pitch[i][l] = sp;
             }
-        pa.pyr = pyr_type(r->p.pyr_dtype);
-        int slot = trace ? trace_begin(r->tr, PANO_TRACE_PYR_DOWN, l, s) : -1;
-        if ((e = launch_pyr_down(pa, s)) != cudaSuccess) return e;
-        if (slot >= 0) trace_end(r->tr, slot, s);
-        ++*kernels;
-    }
+            ps.h0[i] = r->hs[0];
+            ps.w0[i] = r->ws[k][0];
+        }
+    ps.count = 2 * n;
+    ps.nlev = r->nlev;
+    ps.pyr = pyr_type(r->p.pyr_dtype);
+    if ((e = launch_pyramid_rest(ps, first, trace ? &r->tr : nullptr, s, kernels)) != cudaSuccess) return e;
     // LK from the coarsest level to the finest
     for (int l = r->nlev - 1; l >= 0; --l)
         if ((e = enqueue_lk_level(r, c, l, r->tune[l], s, trace, kernels)) != cudaSuccess) return e;

@@ -94,6 +94,22 @@ def test_fused_luma_and_reduce_equal_the_separate_kernels_and_the_oracle(shape, 
     np.testing.assert_allclose(host(Y1), oracle.pyr_down(Yo), rtol=0, atol=1e-6)
 
 
+@pytest.mark.parametrize("shape,nlev", [((300, 200), 6), ((37, 53), 5), ((1, 1), 4), ((130, 17), 7), ((64, 64), 3),
+                                        ((2000, 750), 6)])
+def test_multi_level_reduce_equals_one_level_steps_and_the_oracle(shape, nlev):
+    Y = cuda(rng(33).uniform(0, 1, size=shape).astype(np.float32))
+    got = binding.stage_pyramid(Y, nlev)
+    ref = [Y]
+    for _ in range(nlev - 1):
+        ref.append(binding.stage_pyr_down(ref[-1]))
+    torch.cuda.synchronize()
+    for l, (a, b) in enumerate(zip(got, ref[1:]), start=1):
+        assert torch.equal(a, b), l
+    if shape[0] * shape[1] <= 100000:
+        for a, o in zip(got, oracle.pyramid(host(Y), nlev)[1:]):
+            np.testing.assert_allclose(host(a), o, rtol=0, atol=1e-6)
+
+
 def test_pyr_down_respects_row_pitch():
     big = rng(3).uniform(0, 1, size=(40, 64)).astype(np.float32)
     view = cuda(big)[:, :45]                      # rows of 64 elements, 45 used
