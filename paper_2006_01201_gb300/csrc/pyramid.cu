@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) luma_reduce_kernel(const __grid_constant_
 // pixel (the replicate border), and writes the pixels it owns. Same values
 // as M launches of pyr_down_kernel.
 // ---------------------------------------------------------------------------
-constexpr int kTailTC = 4;
+constexpr int kTailTC = 8;
 // side of the region needed at distance d: n(0) = TC, n(d) = 2 n(d-1) + 3
 __host__ __device__ constexpr int tail_n(int d) { return (kTailTC + 3) * (1 << d) - 3; }
 // offset of the buffer of distance d (the buffers of distances 0 .. d-1 before it)
