@@ -14,7 +14,9 @@
 // level on chip. Because step k at p reads the flows of step k-1 on W(p),
 // the tile carries a halo of K*r pixels that shrinks by r per step; the
 // template, its gradient, the flow and the inverse normal matrices stay in
-// shared memory for the whole level, and only J is gathered from L1/L2. Each
+// shared memory for the whole level, and so does a box of J around the
+// region (shifted by the tile's reference flow); a sample outside the box is
+// gathered from L1/L2. Each
 // step is: per-sample residual products -> column box sums -> row box sums
 // and the 2x2 solve. Both flow directions run in the same launch
 // (blockIdx.z). To keep FP32 rounding independent of the size of the flow,
@@ -28,6 +30,34 @@ namespace pano {
 namespace {
 
 constexpr int kLkThreads = 512;
+constexpr int kTileJM = 4;  // margin of the staged target box around the region, pixels
+
+// The target box of a tile: the region shifted by the integer part of the
+// reference flow, widened by kTileJM on every side (one more column and row
+// for the second bilinear tap).
+__host__ __device__ __forceinline__ int tile_jbw(int rw) { return rw + 2 * kTileJM + 1; }
+__host__ __device__ __forceinline__ int tile_jbh(int rh) { return rh + 2 * kTileJM + 1; }
+
+// J at (qx + ox, qy + oy) as sample_plane computes it (same taps, same
+// weights, same arithmetic), from the staged box when all four taps lie in
+// it and from global memory otherwise.
+template <class Ts>
+__device__ __forceinline__ float sample_box(const float* __restrict__ sJ, int jbw, int jbh, int jx0, int jy0,
+                                            const Ts* __restrict__ J, int pitchJ, int w, int h, int qx, int qy,
+                                            float ox, float oy) {
+    const float cx = fminf(fmaxf(ox, -(float)(w + 2)), (float)(w + 2));
+    const float cy = fminf(fmaxf(oy, -(float)(h + 2)), (float)(h + 2));
+    const float fx = floorf(cx), fy = floorf(cy);
+    const int bx = qx + (int)fx - jx0, by = qy + (int)fy - jy0;
+    if ((unsigned)bx < (unsigned)(jbw - 1) && (unsigned)by < (unsigned)(jbh - 1)) {
+        Taps t;
+        t.ax = cx - fx;
+        t.ay = cy - fy;
+        const float* r0 = sJ + by * jbw + bx;
+        return bilinear_mix(t, r0[0], r0[1], r0[jbw], r0[jbw + 1]);
+    }
+    return sample_plane(J, pitchJ, w, h, qx, qy, ox, oy);
+}
 
 __device__ __forceinline__ float2 start_flow(const LkArgs& a, const LkDir& D, int x, int y) {
     if (a.mode == 0 || D.uin == nullptr) return make_float2(0.f, 0.f);
@@ -61,6 +91,7 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
     float2* sP = sU + N;                                  // per-sample products
     float2* sV = sP + N;                                  // column box sums
     float* sT = reinterpret_cast<float*>(sV + N);         // template
+    float* sJ = sT + N;                                   // staged target box
     const int ox = bx * a.tile_w - halo, oy = by * a.tile_h - halo;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int w = a.w, h = a.h, pitchT = D.pitchT, pitchJ = D.pitchJ;
@@ -95,8 +126,18 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
     const int cy = min(by * a.tile_h + a.tile_h / 2, h - 1);
     const float2 ref = sU[(cy - oy) * RW + (cx - ox)];
 
+    // the staged target box (clamped values), shifted by the reference flow
+    const int jbw = tile_jbw(RW), jbh = tile_jbh(RH);
+    const int jx0 = ox + (int)floorf(fminf(fmaxf(ref.x, -(float)(w + 2)), (float)(w + 2))) - kTileJM;
+    const int jy0 = oy + (int)floorf(fminf(fmaxf(ref.y, -(float)(h + 2)), (float)(h + 2))) - kTileJM;
+
     if (K > 0) {
         __syncthreads();  // everyone has read ref before it is overwritten
+        for (int i = threadIdx.x; i < jbw * jbh; i += blockDim.x) {
+            const int r = i / jbw, c = i - r * jbw;
+            const int yy = min(max(jy0 + r, 0), h - 1), xx = min(max(jx0 + c, 0), w - 1);
+            sJ[i] = ld_f32(J + (long long)yy * pitchJ + xx);
+        }
         // Relative flows and the inverse normal matrices on R_1 (margin RAD).
         for (int ry = warp; ry < RH; ry += nwarps) {
             for (int rx = lane; rx < RW; rx += 32) {
@@ -133,7 +174,8 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
                     if (x >= 0 && x < w && y >= 0 && y < h) {
                         const float2 u = sU[i];
                         const float2 g = sG[i];
-                        const float Jw = sample_plane(J, pitchJ, w, h, x, y, ref.x + u.x, ref.y + u.y);
+                        const float Jw = sample_box(sJ, jbw, jbh, jx0, jy0, J, pitchJ, w, h, x, y, ref.x + u.x,
+                                                    ref.y + u.y);
                         const float It = Jw - sT[i];
                         const float s = fmaf(g.x, u.x, fmaf(g.y, u.y, -It));
                         P = make_float2(g.x * s, g.y * s);
@@ -275,7 +317,8 @@ cudaError_t prepare_tile_t(int max_smem_bytes) {
 size_t lk_smem_bytes(int tile_w, int tile_h, int iters, int radius) {
     size_t halo = (size_t)iters * radius;
     size_t n = (tile_w + 2 * halo) * (tile_h + 2 * halo);
-    return n * (sizeof(float4) + 4 * sizeof(float2) + sizeof(float));
+    const size_t box = sizeof(float) * (size_t)tile_jbw((int)(tile_w + 2 * halo)) * tile_jbh((int)(tile_h + 2 * halo));
+    return n * (sizeof(float4) + 4 * sizeof(float2) + sizeof(float)) + box;
 }
 
 cudaError_t lk_prepare(int max_smem_bytes) {
