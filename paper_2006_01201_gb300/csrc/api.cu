@@ -10,7 +10,10 @@
 #include <string.h>
 
 #include <climits>
+#include <cstdlib>
 #include <new>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "common.cuh"
 #include "pano_flow.h"
@@ -216,6 +219,39 @@ ImageDesc desc(const pano_image* im) {
 }
 
 void set_last_error(const char* msg) { snprintf(g_err, sizeof(g_err), "%s", msg ? msg : ""); }
+
+unsigned debug_flags() {
+    const char* v = getenv("PANO_DEBUG");
+    if (!v) return 0;
+    unsigned f = 0;
+    const char* p = v;
+    while (*p) {
+        const char* q = p;
+        while (*q && *q != ',') ++q;
+        const size_t n = (size_t)(q - p);
+        if (n == 4 && strncmp(p, "sync", 4) == 0) f |= kDebugSync;
+        if (n == 10 && strncmp(p, "fail_alloc", 10) == 0) f |= kDebugFailAlloc;
+        p = *q ? q + 1 : q;
+    }
+    return f;
+}
+
+cudaError_t device_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (debug_flags() & kDebugFailAlloc) return cudaErrorMemoryAllocation;
+    return cudaMalloc(p, bytes);
+}
+
+cudaError_t debug_check(cudaStream_t s) {
+    if (!(debug_flags() & kDebugSync)) return cudaSuccess;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(s);
+    return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+NvtxRange::NvtxRange(const char* name) { nvtxRangePushA(name); }
+NvtxRange::~NvtxRange() { nvtxRangePop(); }
 
 pano_status check_pair_call(const pano_flow_ctx* c, const pano_image* L, const pano_image* R, const float* lr,
                             const float* rl) {
@@ -457,7 +493,7 @@ pano_status pano_flow_create(const pano_flow_params* p, int max_h, int max_w, in
             off[1][d][l] = total;
             total += align_up((size_t)c->flow_pitch[l] * c->lev_h[l] * sizeof(float2), 256);
         }
-    cudaError_t e = cudaMalloc(&c->buf, total);
+    cudaError_t e = device_alloc(&c->buf, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete c;
@@ -486,18 +522,25 @@ pano_status pano_flow_pair(pano_flow_ctx* c, const pano_image* L, const pano_ima
                            float* flow_LtoR, float* flow_RtoL, void* cuda_stream) {
     pano_status st = check_pair_call(c, L, R, flow_LtoR, flow_RtoL);
     if (st != PANO_OK) return st;
+    NvtxRange range("pano_flow_pair");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     PairPlanes pp;
     pair_planes(c, L, R, &pp);
     cudaError_t e;
-    if ((e = launch_pair_pyramid(c, pp, s)) != cudaSuccess) return cuda_fail(e, "pyramid launch");
+    {
+        NvtxRange r("pyramid");
+        if ((e = launch_pair_pyramid(c, pp, s)) != cudaSuccess) return cuda_fail(e, "pyramid launch");
+        if ((e = debug_check(s)) != cudaSuccess) return cuda_fail(e, "pyramid (PANO_DEBUG=sync)");
+    }
     for (int l = c->nlev - 1; l >= 0; --l) {
+        NvtxRange r("LK level");
         LkArgs ka;
         pair_lk_args(c, pp, l, flow_LtoR, flow_RtoL, &ka);
         int t = trace_begin(c->tr, PANO_TRACE_LK, l, s);
         if ((e = launch_lk_level(ka, 2, s)) != cudaSuccess) return cuda_fail(e, "LK launch");
         trace_end(c->tr, t, s);
         c->launches++;
+        if ((e = debug_check(s)) != cudaSuccess) return cuda_fail(e, "LK level (PANO_DEBUG=sync)");
     }
     return PANO_OK;
 }
@@ -529,12 +572,14 @@ pano_status pano_blend_pair(pano_flow_ctx* c, const pano_image* L, const pano_im
     a.F_pitch_bytes = (long long)F->pitch_bytes;
     a.k_sharp = c->p.soft_sharpness;
     a.k_mag = c->p.flow_mag_coef;
+    NvtxRange range("pano_blend_pair");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     int t = trace_begin(c->tr, PANO_TRACE_BLEND, 0, s);
     cudaError_t e = launch_blend(a, s);
     if (e != cudaSuccess) return cuda_fail(e, "blend launch");
     trace_end(c->tr, t, s);
     c->launches++;
+    if ((e = debug_check(s)) != cudaSuccess) return cuda_fail(e, "blend (PANO_DEBUG=sync)");
     return PANO_OK;
 }
 

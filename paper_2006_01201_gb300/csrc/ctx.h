@@ -86,6 +86,24 @@ struct PyrSet {
 };
 cudaError_t launch_pyramid_rest(const PyrSet& ps, int first, Trace* tr, cudaStream_t s, int* kernels);
 
+// PANO_DEBUG: a comma-separated list read from the environment at each call.
+//   sync        synchronise the stream after every stage of a call (outside
+//               stream capture) and report the first failing stage
+//   fail_alloc  make the device allocation of the next create calls fail
+//               (the host-side failure path, without a GPU fault)
+constexpr unsigned kDebugSync = 1u, kDebugFailAlloc = 2u;
+unsigned debug_flags();
+// cudaMalloc, or the simulated failure of PANO_DEBUG=fail_alloc
+cudaError_t device_alloc(void** p, size_t bytes);
+// with PANO_DEBUG=sync: the error of the work enqueued so far on s
+cudaError_t debug_check(cudaStream_t s);
+
+// An NVTX range around a host-side call (shown by profilers; free otherwise).
+struct NvtxRange {
+    explicit NvtxRange(const char* name);
+    ~NvtxRange();
+};
+
 void trace_free(Trace& t);
 pano_status trace_enable(Trace& t, unsigned kind_mask, int capacity);
 pano_status trace_read(Trace& t, pano_trace_record* out, int max_records, int* n_out);

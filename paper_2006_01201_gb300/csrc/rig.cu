@@ -500,7 +500,7 @@ pano_status pano_rig_create(const pano_flow_params* p, const pano_rig_desc* d, p
                 total += align_up((size_t)r->flow_pitch[k][l] * r->hs[l] * 2 * sizeof(float), 256);
             }
         }
-    e = cudaMalloc(&r->buf, total);
+    e = device_alloc(&r->buf, total);
     if (e != cudaSuccess) {
         cudaGetLastError();
         r->buf = nullptr;
@@ -539,11 +539,13 @@ pano_status pano_rig_run(pano_rig* r, const pano_image* L, const pano_image* R, 
     if ((st = check_device(r)) != PANO_OK) return st;
     RunCall c;
     if ((st = fill_call(r, L, R, flow_LtoR, flow_RtoL, canvas, &c)) != PANO_OK) return st;
+    NvtxRange range(use_graph ? "pano_rig_run (graph)" : "pano_rig_run");
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (!use_graph) {
         int kernels = 0;
         cudaError_t e = enqueue_all(r, c, s, true, &kernels);
         r->launches += kernels;
+        if (e == cudaSuccess) e = debug_check(s);
         return e == cudaSuccess ? PANO_OK : cuda_fail(e, "rig launch");
     }
     // a graph captured for these pointers, pitches and tuning, else a new
@@ -564,6 +566,7 @@ pano_status pano_rig_run(pano_rig* r, const pano_image* L, const pano_image* R, 
     }
     r->graphs[g].last_use = ++r->graph_clock;
     cudaError_t e = cudaGraphLaunch(r->graphs[g].exec, s);
+    if (e == cudaSuccess) e = debug_check(s);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphLaunch");
     r->launches += r->graphs[g].kernels;
     return PANO_OK;
