@@ -76,7 +76,7 @@ __device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y, in
 }
 
 template <typename Tv, int C>
-__global__ void __launch_bounds__(256) blend_kernel(BlendArgs a) {
+__global__ void __launch_bounds__(256, 8) blend_kernel(BlendArgs a) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= a.L.w || y >= a.L.h) return;
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) blend_kernel(BlendArgs a) {
 // column, the pair with the highest index owns it; the others skip it, so
 // every canvas pixel has one writer and the result is deterministic.
 template <typename Tv, int C>
-__global__ void __launch_bounds__(256) rig_blend_kernel(const __grid_constant__ RigBlendArgs r) {
+__global__ void __launch_bounds__(256, 8) rig_blend_kernel(const __grid_constant__ RigBlendArgs r) {
     const int p = blockIdx.z;
     const BlendArgs& a = r.pair[p];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
