@@ -320,6 +320,25 @@ PANO_API pano_status pano_stage_lk(const float* T, const float* J, int h, int w,
                           float* flow_out, int iters, int radius, float lambda,
                           void* cuda_stream);
 
+/* Kernel of one LK level (pano_stage_lk_kernel, and per level in the rig of
+ * pano_rig.h). Both kernels compute the same equations with the same order
+ * of FP32 operations; results differ only in rounding, because each tile or
+ * segment measures its flows against its own reference flow. */
+#define PANO_LK_AUTO   0  /* the kernel pano_flow_pair runs for a level of this size: streamed
+                             for levels of at least 50000 pixels (1 <= iters <= 5), tiled
+                             below (16 x 8 tiles below 16000 pixels) */
+#define PANO_LK_STREAM 1  /* streamed row chunks down column bands (1 <= iters <= 5) */
+#define PANO_LK_TILE   2  /* output tiles with a halo of iters * radius pixels */
+
+/* pano_stage_lk with the kernel chosen by the caller (a PANO_LK_* value);
+ * pano_stage_lk itself runs PANO_LK_STREAM when 1 <= iters <= 5, else
+ * PANO_LK_TILE. Errors as pano_stage_lk; INVALID_ARG for an unknown kernel,
+ * UNSUPPORTED for PANO_LK_STREAM outside 1 <= iters <= 5. */
+PANO_API pano_status pano_stage_lk_kernel(const float* T, const float* J, int h, int w, int pitch,
+                                          const float* flow_in, int in_h, int in_w, int upsample,
+                                          float* flow_out, int iters, int radius, float lambda,
+                                          int kernel, void* cuda_stream);
+
 /* Bilinear flow warp, dst(p) = src(p + scale * flow(p)), per channel,
  * clamp-to-edge; Code 1 evaluates it with scale = Blend for L and FlowRtoL
  * and scale = 1 - Blend for R and FlowLtoR. dst: same h, w, c as src,

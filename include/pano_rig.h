@@ -61,15 +61,8 @@ typedef struct pano_rig_desc {
     int canvas_x0[PANO_RIG_MAX_PAIRS];  /* canvas column of strip column 0, in [0, canvas_w) */
 } pano_rig_desc;
 
-/* Kernel of one LK level. */
-#define PANO_LK_AUTO   0  /* per pair, as pano_flow_pair: streamed for levels of at least
-                             50000 pixels (1 <= iters <= 5), tiled below (16 x 8 tiles
-                             below 16000 pixels) */
-#define PANO_LK_STREAM 1  /* streamed kernel for every pair (needs 1 <= iters <= 5) */
-#define PANO_LK_TILE   2  /* tiled kernel for every pair */
-
 typedef struct pano_rig_tuning {
-    int kernel;          /* a PANO_LK_* value */
+    int kernel;          /* a PANO_LK_* value (pano_flow.h) */
     int seg_rows;        /* streamed kernel: rows per segment, 0 = automatic (about 192,
                             rounded to whole waves of the GPU) */
     int tile_w, tile_h;  /* tiled kernel: output tile; both 0 = the default tile */

@@ -90,6 +90,7 @@ SIGNATURES = {
     "pano_stage_luma_pyr": ([_IMG, _VP, _I, _VP, _I, _VP], _I),
     "pano_stage_pyramid": ([_VP, _I, _I, _I, _PP, ctypes.POINTER(ctypes.c_int), _I, _VP], _I),
     "pano_stage_lk": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _VP], _I),
+    "pano_stage_lk_kernel": ([_VP, _VP, _I, _I, _I, _VP, _I, _I, _I, _VP, _I, _I, _F, _I, _VP], _I),
     "pano_stage_warp": ([_IMG, _VP, _F, _IMG, _VP], _I),
     "pano_blend_coeff_scratch_bytes": ([_I, _I], ctypes.c_size_t),
     "pano_blend_coeff": ([_VP, _I, _I, ctypes.c_size_t, _VP, _I, _VP, ctypes.c_size_t, _VP], _I),
@@ -674,7 +675,9 @@ def stage_pyr_down(src, stream=None):
     return dst
 
 
-def stage_lk(T, J, flow_in=None, upsample=False, iters=5, radius=2, lam=1e-2, stream=None):
+def stage_lk(T, J, flow_in=None, upsample=False, iters=5, radius=2, lam=1e-2, stream=None, kernel=None):
+    """One LK level (pano_stage_lk); `kernel` (a PANO_LK_* value) selects the
+    kernel through pano_stage_lk_kernel."""
     torch = _torch()
     for t, n in ((T, "T"), (J, "J")):
         if t.dtype != torch.float32 or t.dim() != 2 or not t.is_contiguous():
@@ -691,8 +694,13 @@ def stage_lk(T, J, flow_in=None, upsample=False, iters=5, radius=2, lam=1e-2, st
         if not upsample and (ih, iw) != (h, w):
             raise PanoError(PANO_ERR_INVALID_ARG, "flow_in must match T unless upsample is set")
         fin = flow_in.data_ptr()
-    _check(load_library().pano_stage_lk(T.data_ptr(), J.data_ptr(), h, w, w, fin, ih, iw, int(bool(upsample)),
-                                        out.data_ptr(), iters, radius, lam, _stream_ptr(stream)))
+    if kernel is None:
+        _check(load_library().pano_stage_lk(T.data_ptr(), J.data_ptr(), h, w, w, fin, ih, iw, int(bool(upsample)),
+                                            out.data_ptr(), iters, radius, lam, _stream_ptr(stream)))
+    else:
+        _check(load_library().pano_stage_lk_kernel(T.data_ptr(), J.data_ptr(), h, w, w, fin, ih, iw,
+                                                   int(bool(upsample)), out.data_ptr(), iters, radius, lam,
+                                                   int(kernel), _stream_ptr(stream)))
     return out
 
 

@@ -688,6 +688,16 @@ pano_status pano_stage_pyr_down(const float* src, int h, int w, int src_pitch, f
 pano_status pano_stage_lk(const float* T, const float* J, int h, int w, int pitch, const float* flow_in,
                           int in_h, int in_w, int upsample, float* flow_out, int iters, int radius,
                           float lambda, void* cuda_stream) {
+    // the stage entry point runs the streamed kernel whenever it applies
+    return pano_stage_lk_kernel(T, J, h, w, pitch, flow_in, in_h, in_w, upsample, flow_out, iters, radius, lambda,
+                                lk_stream_supports(iters, radius) ? PANO_LK_STREAM : PANO_LK_TILE, cuda_stream);
+}
+
+pano_status pano_stage_lk_kernel(const float* T, const float* J, int h, int w, int pitch, const float* flow_in,
+                                 int in_h, int in_w, int upsample, float* flow_out, int iters, int radius,
+                                 float lambda, int kernel, void* cuda_stream) {
+    if (kernel < PANO_LK_AUTO || kernel > PANO_LK_TILE)
+        return fail(PANO_ERR_INVALID_ARG, "kernel %d is not a PANO_LK_* value", kernel);
     if (!T || !J || ((uintptr_t)T) % 4 || ((uintptr_t)J) % 4)
         return fail(PANO_ERR_INVALID_ARG, "T or J NULL or misaligned");
     if (h < 1 || w < 1 || pitch < w) return fail(PANO_ERR_INVALID_ARG, "bad size or pitch");
@@ -696,6 +706,8 @@ pano_status pano_stage_lk(const float* T, const float* J, int h, int w, int pitc
     if (flow_in && ((uintptr_t)flow_in) % 8) return fail(PANO_ERR_INVALID_ARG, "flow_in is not 8-byte aligned");
     if (iters < 0 || iters > 16 || radius < 1 || radius > 3 || !(lambda >= 0.f))
         return fail(PANO_ERR_INVALID_ARG, "iters, radius or lambda out of range");
+    if (kernel == PANO_LK_STREAM && !lk_stream_supports(iters, radius))
+        return fail(PANO_ERR_UNSUPPORTED, "the streamed kernel needs 1 <= iters <= 5");
     int ih = h, iw = w;
     if (flow_in && upsample) {
         if (in_h < 1 || in_w < 1) return fail(PANO_ERR_INVALID_ARG, "coarse flow size %dx%d", in_h, in_w);
@@ -725,9 +737,14 @@ pano_status pano_stage_lk(const float* T, const float* J, int h, int w, int pitc
     ka.iters = iters;
     ka.radius = radius;
     ka.lambda = lambda;
-    // the stage entry point always runs the streamed kernel when it applies
-    cudaError_t e = lk_stream_supports(iters, radius) ? launch_lk_stream(ka, 1, static_cast<cudaStream_t>(cuda_stream))
-                                                      : launch_lk_tile(ka, 1, static_cast<cudaStream_t>(cuda_stream));
+    ka.pyr = kPyrF32;
+    const cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e;
+    switch (kernel) {
+        case PANO_LK_AUTO: e = launch_lk_level(ka, 1, s); break;
+        case PANO_LK_STREAM: e = launch_lk_stream(ka, 1, s); break;
+        default: e = launch_lk_tile(ka, 1, s); break;
+    }
     return e == cudaSuccess ? PANO_OK : cuda_fail(e, "LK launch");
 }
 

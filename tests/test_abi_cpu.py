@@ -102,6 +102,11 @@ def test_calls_reject_null_and_bad_images(lib):
     assert lib.pano_stage_lk(0x1000, 0x2000, 8, 8, 8, 0x3000, 8, 8, 0, 0x3100, 1, 2, 0.01, None) == \
         binding.PANO_ERR_INVALID_ARG   # flow_in overlaps flow_out
     assert b"overlap" in lib.pano_last_error(None)
+    for kernel, st in ((3, binding.PANO_ERR_INVALID_ARG), (-1, binding.PANO_ERR_INVALID_ARG)):
+        assert lib.pano_stage_lk_kernel(0x1000, 0x2000, 8, 8, 8, None, 0, 0, 0, 0x3000, 5, 2, 0.01, kernel,
+                                        None) == st
+    assert lib.pano_stage_lk_kernel(0x1000, 0x2000, 8, 8, 8, None, 0, 0, 0, 0x3000, 0, 2, 0.01,
+                                    binding.PANO_LK_STREAM, None) == binding.PANO_ERR_UNSUPPORTED
 
 
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):

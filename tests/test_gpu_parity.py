@@ -146,6 +146,32 @@ def test_lk_steps_at_one_level_match_oracle():
     assert epe(got, ref).mean() <= 1e-5
 
 
+@pytest.mark.parametrize("kernel", [binding.PANO_LK_AUTO, binding.PANO_LK_STREAM, binding.PANO_LK_TILE])
+@pytest.mark.parametrize("h,w,iters,radius,start", [(230, 317, 5, 2, "coarse"), (121, 203, 3, 1, "given"),
+                                                    (64, 96, 4, 3, "zero"), (3, 5, 5, 2, "coarse")])
+def test_each_lk_kernel_matches_oracle(kernel, h, w, iters, radius, start):
+    # several bands, segments and tiles with ragged edges; each kernel
+    # selected through pano_stage_lk_kernel
+    T = texture(h, w, 11).astype(np.float32)
+    J = (0.8 * np.roll(T, (1, -2), axis=(0, 1)) + 0.2 * texture(h, w, 12)).astype(np.float32)
+    g = rng(13)
+    if start == "coarse":
+        uin = g.normal(0, 1.0, size=((h + 1) // 2, (w + 1) // 2, 2)).astype(np.float32)
+        ref = oracle.upsample_flow(uin, h, w)
+    elif start == "given":
+        uin = g.normal(0, 1.5, size=(h, w, 2)).astype(np.float32)
+        ref = uin.astype(np.float64)
+    else:
+        uin, ref = None, np.zeros((h, w, 2))
+    for _ in range(iters):
+        ref = oracle.lk_step(T, J, ref, radius, 1e-2)
+    got = host(binding.stage_lk(cuda(T), cuda(J), None if uin is None else cuda(uin), upsample=start == "coarse",
+                                iters=iters, radius=radius, lam=1e-2, kernel=kernel))
+    assert np.isfinite(got).all()
+    assert epe(got, ref).mean() <= 1e-5
+    assert np.abs(got - ref).max() <= 1e-3
+
+
 def test_upsample_stage_matches_oracle():
     hc, wc, h, w = 23, 37, 45, 73
     uc = rng(8).normal(0, 2, size=(hc, wc, 2)).astype(np.float32)
