@@ -44,7 +44,13 @@ SMALL_TILE_PIXELS = 16000    # tiled levels below this many pixels use 16 x 8 ti
 # DRAM bytes (read + write) per launch of the dominant kernel, averaged over
 # its launches in one step, from an ncu capture of the current kernel; None
 # when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (1.188352e6 + 4.644352e6 + 18.4704e6 + 171.916032e6) / 4}
+TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (1.188352e6 + 4.644352e6 + 18.469632e6 + 171.617024e6) / 4}
+# Warp instructions per launch of the dominant kernel from the same capture
+# (smsp__inst_executed.sum, averaged over its launches in one step).
+INST_PER_LAUNCH = {"lk_stream_kernel": (10547162 + 32482633 + 90413525 + 366752745) / 4}
+# One warp instruction per scheduler per cycle, four schedulers per SM.
+SCHEDULERS_PER_SM = 4
+SMS = 152
 
 
 # ---------------------------------------------------------------------------
@@ -292,6 +298,19 @@ PAPER_CONTEXT = "under 30 s per 9000x4000 panorama for the whole workflow on an 
 LK_FLOPS_PER_PIXEL_STEP = 50
 
 
+def issue_roofline(kernel: str, launch_ms: float, sm_mhz):
+    """Warp-instruction issue rate of `kernel` (ncu instruction count per
+    launch / live launch time) against the SMs' issue peak at the sampled SM
+    clock; None without a counted instruction total or a clock sample."""
+    inst = INST_PER_LAUNCH.get(kernel)
+    if not inst or not launch_ms or not sm_mhz:
+        return None
+    achieved = inst / (launch_ms * 1e-3) / 1e9
+    peak = SMS * SCHEDULERS_PER_SM * sm_mhz * 1e6 / 1e9
+    return {"achieved": achieved, "peak": peak, "unit": "G warp-instr/s", "frac": achieved / peak,
+            "inst_per_launch": inst, "kernel": kernel, "peak_source": "152 SMs x 4 schedulers x sampled SM clock"}
+
+
 def fp32_peak_tflops(sm_mhz: float = 2070.0, sms: int = 152) -> float:
     """FP32 FMA peak: 128 lanes per SM, 2 flops per FMA."""
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
@@ -457,6 +476,7 @@ def run_gpu(args):
                 "traffic": TRAFFIC_PER_LAUNCH.get(dominant), "kernel": dominant,
                 "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                 "launches_per_step": launches_per_step, "peak_source": f"{peak_src} hbm_gbs"}
+    issue = issue_roofline(dominant, launch_ms, clocks["sm_mhz"] if clocks else None)
     path_bytes = path_alg_bytes(h, w, c, levels, elem=elem)
     path_gbs = path_bytes / (total_ms / args.steps * 1e-3) / 1e9
     stage_bytes = unfused_stage_bytes(h, w, levels, WL["iters"], elem)
@@ -486,7 +506,7 @@ def run_gpu(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(WL, l2="flushed between steps (256 MB write, untimed)",
                                parallelism=f"replicas{world}", pyr_dtype=args.pyr_dtype),
-                "roofline": roofline,
+                "roofline": roofline, "issue_roofline": issue,
                 "path": {"alg_bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / peak,
                          "unfused_stage_bytes_per_step": stage_bytes,
                          "fp32_tflops": path_flops / (total_ms / args.steps * 1e-3) / 1e12,
@@ -784,6 +804,7 @@ def run_rig(args):
                 "traffic": TRAFFIC_PER_LAUNCH.get(dominant), "kernel": dominant,
                 "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                 "launches_per_step": dk["launches"] / args.steps, "peak_source": f"{peak_src} hbm_gbs"}
+    issue = issue_roofline(dominant, launch_ms, clocks["sm_mhz"] if clocks else None)
     path_bytes = sum(path_alg_bytes(h, w, c, levels, elem=elem) for w in widths)
 
     def time_rig(other):
@@ -862,7 +883,7 @@ def run_rig(args):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(W, l2="flushed between steps (256 MB write, untimed); inputs 262 MB > L2",
                                parallelism=f"replicas{world}", graph=True, pyr_dtype=args.pyr_dtype),
-                "roofline": roofline,
+                "roofline": roofline, "issue_roofline": issue,
                 "path": {"alg_bytes_per_step": path_bytes,
                          "achieved_gbs": path_bytes / (total_ms / args.steps * 1e-3) / 1e9},
                 "kernels": per_kind, "dominant_kernel": dominant,

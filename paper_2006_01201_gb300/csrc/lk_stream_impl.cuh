@@ -60,7 +60,6 @@ template <int RAD, int K, int BW, int CH>
 struct StreamGeom {
     static constexpr int RW = BW + 2 * K * RAD;  // region columns
     static constexpr int JW = RW + 2 * kMX + 2;  // target box columns
-    static constexpr int JRS = 2 * ((JW + 1) / 2);  // ring row: even box columns, then odd ones
     static constexpr int PR = CH + 2 * RAD;      // rows of the product buffer
     static_assert(CH >= 2 * RAD, "chunk must cover the column-sum history");
     static_assert(CH + (K + 1) * RAD <= kRing, "row ring too small");
@@ -71,7 +70,7 @@ struct StreamGeom {
     static constexpr size_t kGiA = kU + sizeof(float2) * kRing * RW;
     static constexpr size_t kGiB = kGiA + sizeof(float2) * kRing * RW;
     static constexpr size_t kJ = kGiB + sizeof(float) * kRing * RW;
-    static constexpr size_t kP = kJ + sizeof(float) * kRing * JRS;
+    static constexpr size_t kP = kJ + sizeof(float) * kRing * JW;
     static constexpr size_t kH = kP + sizeof(float2) * PR * RW;
     static constexpr size_t kV = kH + sizeof(float2) * K * 2 * RAD * RW;
     static constexpr size_t kCSA = kV + sizeof(float2) * CH * RW;
@@ -85,15 +84,6 @@ struct StreamGeom {
 };
 
 __device__ __forceinline__ int ring_slot(int y) { return (y + kRingOff) & (kRing - 1); }
-
-// A row of the target ring holds the even box columns first and the odd ones
-// after them: the two taps of a sample are then one element of each half,
-// and the lanes of a warp (which sample pixels two columns apart) read
-// consecutive words of each half, on distinct banks.
-template <int JW>
-__device__ __forceinline__ int jcol(int bc) {
-    return (bc & 1) ? (JW + 1) / 2 + (bc >> 1) : (bc >> 1);
-}
 
 // Paired FP32 arithmetic (one instruction for the two lanes of a float2;
 // each lane rounds exactly as the scalar operation would).
@@ -149,11 +139,9 @@ __device__ __forceinline__ float sample_target(const TargetBox<Ts>& b, int x, in
         Taps t;
         t.ax = ox - fx;
         t.ay = oy - fy;
-        constexpr int JRS = 2 * ((JW + 1) / 2);
-        const int c0 = jcol<JW>(bcol), c1 = jcol<JW>(bcol + 1);
-        const float* r0 = b.sJ + ring_slot(y + iy) * JRS;
-        const float* r1 = b.sJ + ring_slot(y + iy + 1) * JRS;
-        return bilinear_mix(t, r0[c0], r0[c1], r1[c0], r1[c1]);
+        const float* r0 = b.sJ + ring_slot(y + iy) * JW + bcol;
+        const float* r1 = b.sJ + ring_slot(y + iy + 1) * JW + bcol;
+        return bilinear_mix(t, r0[0], r0[1], r1[0], r1[1]);
     }
     // outside the staged box (large or non-finite offsets): clamped global taps
     return sample_plane(b.J, b.pitchJ, b.w, b.h, x, y, ox, oy);
@@ -205,7 +193,6 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
     using Geo = StreamGeom<RAD, K, BW, CH>;
     constexpr int RW = Geo::RW;
     constexpr int JW = Geo::JW;
-    constexpr int JRS = Geo::JRS;
     // Thread layout: thread (ty, tx) works on row ty of every chunk-sized
     // block of rows and on the columns tx, tx + TX, tx + 2 TX, ...
     constexpr int TX = kStreamThreads / CH;
@@ -301,7 +288,7 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
             const int yy = i / JW, bc = i - yy * JW;
             const int yj = yb + yy;
             const int ys = min(max(yj, 0), h - 1), xs = min(max(jx0 + bc, 0), w - 1);
-            sJ[ring_slot(yj) * JRS + jcol<JW>(bc)] = ld_f32(box.J + (long long)ys * box.pitchJ + xs);
+            sJ[ring_slot(yj) * JW + bc] = ld_f32(box.J + (long long)ys * box.pitchJ + xs);
         }
     }
     copy_async_wait_all();
@@ -395,9 +382,8 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                 const int yj = a0 + CH + box.fref_y + kMY + 1 + ty;
                 const Ts* jsrc = box.J + (long long)min(max(yj, 0), h - 1) * box.pitchJ;
                 if constexpr (kAsyncT) {
-                    float* jdst = sJ + ring_slot(yj) * JRS;
-                    for (int bc = tx; bc < JW; bc += TX)
-                        copy_async4(jdst + jcol<JW>(bc), jsrc + min(max(jx0 + bc, 0), w - 1));
+                    float* jdst = sJ + ring_slot(yj) * JW;
+                    for (int bc = tx; bc < JW; bc += TX) copy_async4(jdst + bc, jsrc + min(max(jx0 + bc, 0), w - 1));
                     copy_async_commit();
                 } else {
 #pragma unroll
@@ -447,30 +433,16 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                     float2 ga0, ga1;
                     float gb0, gb1;
                     if (k == 1) {
-                        // the 2 HR + 2 column sums around the pair, read with 16-byte
-                        // (c11, c12) and 8-byte (c22) loads that the lanes of a warp
-                        // take from consecutive addresses
-                        const float4* caq = reinterpret_cast<const float4*>(sCSA + ty * RW + xp - HR);
-                        const float2* cbq = reinterpret_cast<const float2*>(sCSB + ty * RW + xp - HR);
-                        float2 ca[2 * HR + 2];
-                        float cb[2 * HR + 2];
-#pragma unroll
-                        for (int q = 0; q < NPAIR; ++q) {
-                            const float4 t4 = caq[q];
-                            ca[2 * q] = make_float2(t4.x, t4.y);
-                            ca[2 * q + 1] = make_float2(t4.z, t4.w);
-                            const float2 t2 = cbq[q];
-                            cb[2 * q] = t2.x;
-                            cb[2 * q + 1] = t2.y;
-                        }
+                        const float2* ca = sCSA + ty * RW + xp;
+                        const float* cb = sCSB + ty * RW + xp;
                         float2 a1 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);  // (x11, x12)
                         float a22 = 0.f, b22 = 0.f;
 #pragma unroll
                         for (int d = -RAD; d <= RAD; ++d) {
-                            a1 = add2(a1, ca[HR + d]);
-                            a22 += cb[HR + d];
-                            b1 = add2(b1, ca[HR + d + 1]);
-                            b22 += cb[HR + d + 1];
+                            a1 = add2(a1, ca[d]);
+                            a22 += cb[d];
+                            b1 = add2(b1, ca[d + 1]);
+                            b22 += cb[d + 1];
                         }
                         const float a11 = a1.x, a12 = a1.y, b11 = b1.x, b12 = b1.y;
                         const float p11 = a11 + lam, p22 = a22 + lam;
@@ -529,11 +501,11 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                 if constexpr (!kAsyncT) {
                     // the target loads issued before X_K land in the ring now
                     const int yj = a0 + CH + box.fref_y + kMY + 1 + ty;
-                    float* jdst = sJ + ring_slot(yj) * JRS;
+                    float* jdst = sJ + ring_slot(yj) * JW;
 #pragma unroll
                     for (int q = 0; q < kJPT; ++q) {
                         const int bc = tx + q * TX;
-                        if (bc < JW) jdst[jcol<JW>(bc)] = jnext[q];
+                        if (bc < JW) jdst[bc] = jnext[q];
                     }
                 }
             }
