@@ -16,6 +16,18 @@ def test_level_pixels_and_lk_bytes():
     assert b[1] == 2 * (8 * 1_500_000 + 8 * 1_500_000)
 
 
+def test_issue_roofline_against_the_schedulers_peak():
+    # 1.2587e11 warp instructions per second = 152 SMs x 4 schedulers x 2070 MHz / 10
+    inst = bench.INST_PER_LAUNCH["lk_stream_kernel"]
+    launch_ms = inst / (0.1 * 152 * 4 * 2070e6) * 1e3
+    r = bench.issue_roofline("lk_stream_kernel", launch_ms, 2070.0)
+    assert r["peak"] == pytest.approx(152 * 4 * 2.07)
+    assert r["frac"] == pytest.approx(0.1)
+    # no instruction count, no clock sample: no figure
+    assert bench.issue_roofline("blend_kernel", 1.0, 2070.0) is None
+    assert bench.issue_roofline("lk_stream_kernel", 1.0, None) is None
+
+
 def test_throughput_counts_every_rank():
     # 6 MP per step, 10 steps, 2 ranks, slowest rank 20 ms in total
     assert bench.throughput(6_000_000, 10, 2, 20.0) == pytest.approx(6000.0)
