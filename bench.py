@@ -42,8 +42,9 @@ L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 STREAM_MIN_PIXELS = 50000    # levels with at least this many pixels use the streamed LK kernel
 SMALL_TILE_PIXELS = 16000    # tiled levels below this many pixels use 16 x 8 tiles
 # DRAM bytes (read + write) per launch of the dominant kernel, averaged over
-# its launches in one step, from an ncu capture of the current kernel; None
-# when the kernel has changed since the counters were taken.
+# its launches in one step, from an ncu capture of the current kernel with
+# float32 pyramid planes (the 16-bit instantiations are other kernels: no
+# figure); None when the kernel has changed since the counters were taken.
 TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (1.188352e6 + 4.644352e6 + 18.469632e6 + 171.617024e6) / 4}
 # Warp instructions per launch of the dominant kernel from the same capture
 # (smsp__inst_executed.sum, averaged over its launches in one step).
@@ -473,10 +474,11 @@ def run_gpu(args):
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9 if bytes_per_launch else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": TRAFFIC_PER_LAUNCH.get(dominant), "kernel": dominant,
+                "traffic": TRAFFIC_PER_LAUNCH.get(dominant) if args.pyr_dtype == "f32" else None, "kernel": dominant,
                 "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                 "launches_per_step": launches_per_step, "peak_source": f"{peak_src} hbm_gbs"}
-    issue = issue_roofline(dominant, launch_ms, clocks["sm_mhz"] if clocks else None)
+    issue = issue_roofline(dominant, launch_ms, clocks["sm_mhz"] if clocks else None) \
+        if args.pyr_dtype == "f32" else None
     path_bytes = path_alg_bytes(h, w, c, levels, elem=elem)
     path_gbs = path_bytes / (total_ms / args.steps * 1e-3) / 1e9
     stage_bytes = unfused_stage_bytes(h, w, levels, WL["iters"], elem)
@@ -801,10 +803,11 @@ def run_rig(args):
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9 if bytes_per_launch else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": TRAFFIC_PER_LAUNCH.get(dominant), "kernel": dominant,
+                "traffic": TRAFFIC_PER_LAUNCH.get(dominant) if args.pyr_dtype == "f32" else None, "kernel": dominant,
                 "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                 "launches_per_step": dk["launches"] / args.steps, "peak_source": f"{peak_src} hbm_gbs"}
-    issue = issue_roofline(dominant, launch_ms, clocks["sm_mhz"] if clocks else None)
+    issue = issue_roofline(dominant, launch_ms, clocks["sm_mhz"] if clocks else None) \
+        if args.pyr_dtype == "f32" else None
     path_bytes = sum(path_alg_bytes(h, w, c, levels, elem=elem) for w in widths)
 
     def time_rig(other):
