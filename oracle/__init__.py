@@ -73,6 +73,7 @@ def lib():
                                       None),
             "oracle_blend": ([_D, _D, i, i, i, _D, _D, _D, d, d, _D], None),
             "oracle_blend_weights": ([i, i, _D, _D, _D, d, d, _D, _D], None),
+            "oracle_compose": ([_D, _D, i, i, i, _U8, _D, _D, _D, i, i, i, i, d, d, _D], None),
             "oracle_quantize_u8": ([_D, l, _U8], None),
             "oracle_energy": ([_D, _D, i, i, _D, d], d),
             "oracle_energy_grad": ([_D, _D, i, i, _D, d, _D, _D, _D], None),
@@ -292,6 +293,24 @@ def blend(L: np.ndarray, R: np.ndarray, flowLR: np.ndarray, flowRL: np.ndarray,
     out = np.empty(a.shape, dtype=np.float64)
     lib().oracle_blend(_d(a), _d(b), h, w, c, _d(lr), _d(rl), None if bl is None else _d(bl),
                        p.soft_sharpness, p.flow_mag_coef, _d(out))
+    return out
+
+
+def compose(L: np.ndarray, R: np.ndarray, label: np.ndarray, blend_arr: np.ndarray, flowLR: np.ndarray,
+            flowRL: np.ndarray, origin, p: Params) -> np.ndarray:
+    """Code 1 on a canvas (every branch) on unit-scaled inputs; returns F
+    (float64, same shape as L). origin = (row, column) of the flows' crop."""
+    a, b = to_unit(L), to_unit(R)
+    h, w = a.shape[:2]
+    c = 1 if a.ndim == 2 else a.shape[2]
+    lab = np.ascontiguousarray(label, dtype=np.uint8)
+    assert lab.shape == (h, w)
+    bl = _f64(blend_arr)
+    lr, rl = _f64(flowLR), _f64(flowRL)
+    fh, fw = lr.shape[:2]
+    out = np.empty(a.shape, dtype=np.float64)
+    lib().oracle_compose(_d(a), _d(b), h, w, c, lab.ctypes.data_as(_U8), _d(bl), _d(lr), _d(rl),
+                         int(origin[0]), int(origin[1]), fh, fw, p.soft_sharpness, p.flow_mag_coef, _d(out))
     return out
 
 

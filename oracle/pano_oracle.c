@@ -527,6 +527,62 @@ void oracle_blend(const double* L, const double* R, int h, int w, int c, const d
         }
 }
 
+/* ---------------------------------------------------------------------------
+ * Code 1 on a whole canvas (Section III-C-3), every branch:
+ *   Area1 (label 1): F = L(p);  Area2 (label 2): F = R(p);
+ *   Area3 (label 3): the blend above, with L and R the canvas images;
+ *   any other label: F = 0.
+ * L, R: (h, w, c) unit-scaled canvas images. label: (h, w). blend: (h, w),
+ * Eq. (1). flowLR, flowRL: (fh, fw, 2), the flows of the overlap crop whose
+ * pixel (0, 0) is canvas pixel (fy0, fx0).
+ * Readings: the Area3 samples read the canvas images (clamp-to-edge at the
+ * canvas border), so a displaced sample near the seam reads L or R beyond
+ * the crop, as Code 1 samples the images L and R themselves. FlowMag divides
+ * by the crop width fw, the overlap width of the strip form. An Area3 pixel
+ * outside the crop has no flow and uses zero.
+ * ------------------------------------------------------------------------- */
+void oracle_compose(const double* L, const double* R, int h, int w, int c, const unsigned char* label,
+                    const double* blend, const double* flowLR, const double* flowRL, int fy0, int fx0, int fh,
+                    int fw, double k_sharp, double k_mag, double* F)
+{
+#pragma omp parallel for schedule(static)
+    for (int y = 0; y < h; ++y)
+        for (int x = 0; x < w; ++x) {
+            size_t p = (size_t)y * w + x;
+            double* out = F + p * c;
+            unsigned char area = label[p];
+            if (area == 1) {                      /* Code 1: F(i, j) = L(i, j) */
+                for (int ch = 0; ch < c; ++ch) out[ch] = L[p * c + ch];
+            } else if (area == 2) {               /* Code 1: F(i, j) = R(i, j) */
+                for (int ch = 0; ch < c; ++ch) out[ch] = R[p * c + ch];
+            } else if (area == 3) {
+                /* FlowRtoL(i, j), FlowLtoR(i, j) from the crop (zero outside it) */
+                double rtol_x = 0.0, rtol_y = 0.0, ltor_x = 0.0, ltor_y = 0.0;
+                int qy = y - fy0, qx = x - fx0;
+                if (qy >= 0 && qy < fh && qx >= 0 && qx < fw) {
+                    size_t q = 2 * ((size_t)qy * fw + qx);
+                    rtol_x = flowRL[q];
+                    rtol_y = flowRL[q + 1];
+                    ltor_x = flowLR[q];
+                    ltor_y = flowLR[q + 1];
+                }
+                double BlendL = 1.0 - blend[p], BlendR = blend[p];
+                double Lx_ = x + (1.0 - BlendL) * rtol_x, Ly_ = y + (1.0 - BlendL) * rtol_y;
+                double Rx_ = x + (1.0 - BlendR) * ltor_x, Ry_ = y + (1.0 - BlendR) * ltor_y;
+                double FlowMagRL = sqrt(rtol_x * rtol_x + rtol_y * rtol_y) / (double)fw;
+                double FlowMagLR = sqrt(ltor_x * ltor_x + ltor_y * ltor_y) / (double)fw;
+                double FlowL = 1.0 + k_mag * FlowMagRL, FlowR = 1.0 + k_mag * FlowMagLR;
+                double ExpL = exp(k_sharp * BlendL * FlowL), ExpR = exp(k_sharp * BlendR * FlowR);
+                double SoftmaxL = ExpL / (ExpL + ExpR), SoftmaxR = ExpR / (ExpL + ExpR);
+                for (int ch = 0; ch < c; ++ch)
+                    out[ch] = bilinear_strided(L + ch, h, w, c, Lx_, Ly_) * SoftmaxL +
+                              bilinear_strided(R + ch, h, w, c, Rx_, Ry_) * SoftmaxR;
+            } else {                              /* Code 1: F(i, j) = 0 */
+                for (int ch = 0; ch < c; ++ch) out[ch] = 0.0;
+            }
+        }
+}
+
 /* Blend weights alone (for tests): sL, sR per pixel. */
 void oracle_blend_weights(int h, int w, const double* flowLR, const double* flowRL,
                           const double* blend, double k_sharp, double k_mag, double* sL, double* sR)

@@ -12,6 +12,7 @@ import subprocess
 import pytest
 
 import oracle
+from tests import test_oracle_compose_pins as cpins
 from tests import test_oracle_pins as pins
 from tests import test_oracle_refine_pins as rpins
 from tests import test_oracle_storage_pins as spins
@@ -56,6 +57,14 @@ MUTANTS = [
     ("stored level not rounded", "        oracle_round_storage(cur, (long)hs[l] * ws[l], fmt);\n", "\n"),
     ("reduce adjoint weight", "PIX(gsrc, w, sy, sx) += k[ty + 2] * k[tx + 2] * g;",
      "PIX(gsrc, w, sy, sx) += k[ty + 2] * k[ty + 2] * g;"),
+    ("compose Area1 copies R", "/* Code 1: F(i, j) = L(i, j) */\n                for (int ch = 0; ch < c; ++ch) out[ch] = L[p * c + ch];",
+     "/* Code 1: F(i, j) = L(i, j) */\n                for (int ch = 0; ch < c; ++ch) out[ch] = R[p * c + ch];"),
+    ("compose crop origin sign", "int qy = y - fy0, qx = x - fx0;", "int qy = y + fy0, qx = x - fx0;"),
+    ("compose ColorR with FlowRtoL", "double Rx_ = x + (1.0 - BlendR) * ltor_x", "double Rx_ = x + (1.0 - BlendR) * rtol_x"),
+    ("compose FlowMag over canvas width", "double FlowMagRL = sqrt(rtol_x * rtol_x + rtol_y * rtol_y) / (double)fw;",
+     "double FlowMagRL = sqrt(rtol_x * rtol_x + rtol_y * rtol_y) / (double)w;"),
+    ("compose neither not zero", "/* Code 1: F(i, j) = 0 */\n                for (int ch = 0; ch < c; ++ch) out[ch] = 0.0;",
+     "/* Code 1: F(i, j) = 0 */\n                for (int ch = 0; ch < c; ++ch) out[ch] = 0.5;"),
 ]
 
 PIN_TESTS = [
@@ -81,6 +90,11 @@ PIN_TESTS = [
     lambda: rpins.test_smoothness_energy_closed_form(),
     lambda: rpins.test_energy_and_gradients_vanish_on_identical_images_and_zero_flow(),
     lambda: [rpins.test_reduce_transpose_dot_product_identity(s) for s in [(7, 9), (13, 2)]],
+    lambda: cpins.test_area1_area2_and_neither_are_copies_and_zeros(),
+    lambda: [cpins.test_area3_constant_translation_closed_form(d) for d in [(2, -1)]],
+    lambda: cpins.test_swapping_the_roles_of_L_and_R_is_exact(),
+    lambda: cpins.test_crop_origin_places_the_flows_on_the_canvas(),
+    lambda: cpins.test_strip_canvas_reduces_to_the_strip_form(),
     lambda: spins.test_binary16_rounding_matches_numpy(),
     lambda: spins.test_bfloat16_rounding_matches_torch_on_float32_inputs(),
     lambda: spins.test_ties_go_to_the_even_neighbour(),
