@@ -930,6 +930,83 @@ def run_rig(args):
     return 0
 
 
+def run_compose(args):
+    """Code 1 on a whole canvas (pano_compose_pair): a 4000x3000 RGB u8 canvas
+    holding Area1 (750 columns), the 4000x1500 overlap of the benchmark pair
+    (Area3) and Area2 (750 columns). Times the canvas pass alone and the whole
+    stitch of the pair onto the canvas (pano_flow_pair on the overlap crop,
+    then pano_compose_pair)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2006_01201_gb300 as pkg
+    from paper_2006_01201_gb300 import binding, build as gpu_build
+
+    gpu_build.build()
+    pkg.load_library()
+    dev = torch.device("cuda", 0)
+    pair = synth.pair_fullres_rgb()
+    h, ws = pair.shape
+    m = 750
+    w = ws + 2 * m
+    g = np.random.default_rng(7)
+    L = np.concatenate([g.integers(0, 256, (h, m, 3), dtype=np.uint8), pair.L, pair.L[:, -m:][:, ::-1]], 1)
+    R = np.concatenate([pair.R[:, :m][:, ::-1], pair.R, g.integers(0, 256, (h, m, 3), dtype=np.uint8)], 1)
+    lab = np.full((h, w), 3, np.uint8)
+    lab[:, :m], lab[:, m + ws:] = 1, 2
+    Ld, Rd = torch.from_numpy(np.ascontiguousarray(L)).to(dev), torch.from_numpy(np.ascontiguousarray(R)).to(dev)
+    labd = torch.from_numpy(lab).to(dev)
+    Bd = binding.blend_coeff(labd)
+    params = binding.Params(levels=WORKLOAD["levels"])
+    ctx = binding.FlowContext(params, max_h=h, max_w=ws, max_c=3)
+    Lc, Rc = Ld[:, m:m + ws], Rd[:, m:m + ws]
+    lr, rl = ctx.flow_pair(Lc, Rc)
+    F = binding.compose_pair(Ld, Rd, labd, Bd, lr, rl, origin=(0, m), params=params)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record()
+            fn()
+            ev[k][1].record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / args.steps
+
+    ms = timed(lambda: binding.compose_pair(Ld, Rd, labd, Bd, lr, rl, origin=(0, m), params=params, out=F))
+
+    def stitch():
+        ctx.flow_pair(Lc, Rc, out=(lr, rl))
+        binding.compose_pair(Ld, Rd, labd, Bd, lr, rl, origin=(0, m), params=params, out=F)
+
+    ms_stitch = timed(stitch)
+    ctx.close()
+    # per canvas pixel: label 1 B; Area1/Area2 copy 3 B in, 3 B out; Area3 Blend 4 B,
+    # L and R 3 B each, both flows 16 B, F 3 B
+    alg = h * (2 * m) * (1 + 3 + 3) + h * ws * (1 + 4 + 6 + 16 + 3)
+    peak, src = read_peaks()
+    gbs = alg / (ms * 1e-3) / 1e9
+    line = {"metric": "canvas megapixels/sec (Code 1, every branch, on one GB300)",
+            "value": h * w / (ms * 1e-3) / 1e6, "unit": "MP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "compose_4000x3000_rgb_u8_overlap_1500", "area1_cols": m, "area3_cols": ws,
+                       "area2_cols": m, "l2": "flushed between steps (256 MB write, untimed)"},
+            "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                         "traffic": None, "kernel": "compose_kernel", "alg_bytes_per_launch": alg,
+                         "peak_source": f"{src} hbm_gbs"},
+            "stitch": {"metric": "overlap megapixels/sec (flow of the overlap + Code 1 on the canvas)",
+                       "value": h * ws / (ms_stitch * 1e-3) / 1e6, "unit": "MP/s", "ms_per_step": ms_stitch},
+            "gpu_launches": 1}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -938,10 +1015,11 @@ def main(argv=None):
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--cpu-budget", type=float, default=12.0, help="seconds of oracle work for cpu_baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="pair", choices=["pair", "small", "rig", "refine_1024", "blend_coeff"],
+    ap.add_argument("--workload", default="pair",
+                    choices=["pair", "small", "rig", "refine_1024", "blend_coeff", "compose"],
                     help="pair: the 4000x1500 overlap pair (default); small: the 256x512 gray pair; "
                          "rig: the 8-pair 360-degree rig; refine_1024: the differentiable refinement; "
-                         "blend_coeff: general-mask Eq. (1)")
+                         "blend_coeff: general-mask Eq. (1); compose: Code 1 on a 4000x3000 canvas")
     ap.add_argument("--no-autotune", action="store_true", help="rig: keep the default tuning")
     ap.add_argument("--pyr-dtype", default="f32", choices=sorted(PYR_DTYPES),
                     help="storage of the pyramid levels (arithmetic stays FP32)")
@@ -956,6 +1034,8 @@ def main(argv=None):
         return run_rig(args)
     if args.workload == "blend_coeff":
         return run_blend_coeff(args)
+    if args.workload == "compose":
+        return run_compose(args)
     return run_gpu(args)
 
 

@@ -140,6 +140,33 @@ PANO_API pano_status pano_blend_pair(pano_flow_ctx* ctx, const pano_image* L, co
                             const float* flow_LtoR, const float* flow_RtoL, const float* blend,
                             pano_image* F, void* cuda_stream);
 
+/* Code 1 (Section III-C-3) on a whole canvas, every branch, for every pixel p:
+ *   label(p) == 1 (Area1): F(p) = L(p);   label(p) == 2 (Area2): F(p) = R(p);
+ *   label(p) == 3 (Area3): the blend of pano_blend_pair at p, with L and R
+ *                          the canvas images (samples clamp at the canvas
+ *                          border, not at the overlap's);
+ *   any other label:       F(p) = 0.
+ * L, R, F: canvas images (device data), same h, w, c (1 or 3) and dtype
+ *   (PANO_U8 or PANO_F32); values of L and R outside their own areas are
+ *   read only where an Area3 sample lands there.
+ * label: h x w bytes, row pitch label_pitch bytes (the label canvas of
+ *   pano_blend_coeff). blend: h x w float32 Blend values of Eq. (1), row
+ *   pitch blend_pitch floats (e.g. from pano_blend_coeff).
+ * flow_LtoR, flow_RtoL: (flow_h, flow_w, 2) float32 contiguous, the flows of
+ *   the overlap crop whose pixel (0, 0) is canvas pixel (flow_y0, flow_x0),
+ *   as pano_flow_pair gives them for that crop of L and R. FlowMag divides by
+ *   flow_w, the overlap width. An Area3 pixel outside the crop uses zero flow.
+ * params: only soft_sharpness and flow_mag_coef are read.
+ * F must not overlap any input. No allocation; asynchronous on cuda_stream.
+ * Errors: INVALID_ARG (NULL or misaligned pointers, sizes that differ, a crop
+ * outside the canvas, overlapping F), UNSUPPORTED (16-bit or >3-channel
+ * images), CUDA. */
+PANO_API pano_status pano_compose_pair(const pano_flow_params* params, const pano_image* L,
+                                       const pano_image* R, const unsigned char* label, size_t label_pitch,
+                                       const float* blend, int blend_pitch, const float* flow_LtoR,
+                                       const float* flow_RtoL, int flow_y0, int flow_x0, int flow_h,
+                                       int flow_w, pano_image* F, void* cuda_stream);
+
 /* Free the context and its scratch. NULL is accepted. Work already enqueued
  * that uses the context must have completed. */
 PANO_API pano_status pano_flow_destroy(pano_flow_ctx* ctx);

@@ -77,6 +77,7 @@ SIGNATURES = {
     "pano_flow_create": ([_PAR, _I, _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
     "pano_flow_pair": ([_VP, _IMG, _IMG, _VP, _VP, _VP], _I),
     "pano_blend_pair": ([_VP, _IMG, _IMG, _VP, _VP, _VP, _IMG, _VP], _I),
+    "pano_compose_pair": ([_PAR, _IMG, _IMG, _VP, ctypes.c_size_t, _VP, _I, _VP, _VP, _I, _I, _I, _I, _IMG, _VP], _I),
     "pano_flow_destroy": ([_VP], _I),
     "pano_last_error": ([_VP], ctypes.c_char_p),
     "pano_trace_enable": ([_VP, ctypes.c_uint, _I], _I),
@@ -422,6 +423,39 @@ class RigHostPipeline(_Pipeline):
             canvas_host.copy_(buf["canvas"], non_blocking=True)
 
         return self._submit(k, upload, compute, download)
+
+
+def compose_pair(L, R, label, blend, flow_LtoR, flow_RtoL, origin=(0, 0), params: Optional[Params] = None,
+                 out=None, stream=None):
+    """Code 1 on a whole canvas (pano_compose_pair): Area1 (label 1) from L,
+    Area2 (label 2) from R, Area3 (label 3) blended with the flows of the
+    overlap crop whose pixel (0, 0) is canvas pixel `origin`, zero elsewhere.
+    L, R: canvas images; label: (H, W) uint8; blend: (H, W) float32 (Eq. 1)."""
+    torch = _torch()
+    dl, dr = image_desc(L), image_desc(R)
+    if out is None:
+        out = torch.empty_like(L)
+    df = image_desc(out)
+    if label.dtype != torch.uint8 or label.dim() != 2 or label.stride(1) != 1:
+        raise PanoError(PANO_ERR_INVALID_ARG, "label must be a uint8 (H, W) tensor with contiguous rows")
+    if blend.dtype != torch.float32 or blend.dim() != 2 or blend.stride(1) != 1:
+        raise PanoError(PANO_ERR_INVALID_ARG, "blend must be a float32 (H, W) tensor with contiguous rows")
+    if tuple(label.shape) != (dl.h, dl.w) or tuple(blend.shape) != (dl.h, dl.w):
+        raise PanoError(PANO_ERR_INVALID_ARG, "label and blend must have the canvas size")
+    for f, n in ((flow_LtoR, "flow_LtoR"), (flow_RtoL, "flow_RtoL")):
+        if f.dtype != torch.float32 or f.dim() != 3 or f.shape[2] != 2 or not f.is_contiguous():
+            raise PanoError(PANO_ERR_INVALID_ARG, f"{n} must be a contiguous float32 (h, w, 2) tensor")
+    if flow_LtoR.shape != flow_RtoL.shape:
+        raise PanoError(PANO_ERR_INVALID_ARG, "the two flows differ in size")
+    fh, fw = flow_LtoR.shape[0], flow_LtoR.shape[1]
+    p = (params or Params()).to_c()
+    lp = label.stride(0) if dl.h > 1 else dl.w
+    bp = blend.stride(0) if dl.h > 1 else dl.w
+    _check(load_library().pano_compose_pair(ctypes.byref(p), ctypes.byref(dl), ctypes.byref(dr), label.data_ptr(),
+                                            lp, blend.data_ptr(), bp, flow_LtoR.data_ptr(), flow_RtoL.data_ptr(),
+                                            int(origin[0]), int(origin[1]), fh, fw, ctypes.byref(df),
+                                            _stream_ptr(stream)))
+    return out
 
 
 def flow_pair_static(params: Params, L, R, out=None, stream=None):

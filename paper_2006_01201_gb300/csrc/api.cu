@@ -583,6 +583,61 @@ pano_status pano_blend_pair(pano_flow_ctx* c, const pano_image* L, const pano_im
     return PANO_OK;
 }
 
+pano_status pano_compose_pair(const pano_flow_params* p, const pano_image* L, const pano_image* R,
+                              const unsigned char* label, size_t label_pitch, const float* blend, int blend_pitch,
+                              const float* flow_LtoR, const float* flow_RtoL, int flow_y0, int flow_x0,
+                              int flow_h, int flow_w, pano_image* F, void* cuda_stream) {
+    if (!p) return fail(PANO_ERR_INVALID_ARG, "params is NULL");
+    if (!(p->soft_sharpness > -1e30f && p->soft_sharpness < 1e30f) || !(p->flow_mag_coef > -1e30f && p->flow_mag_coef < 1e30f))
+        return fail(PANO_ERR_INVALID_ARG, "soft_sharpness and flow_mag_coef must be finite");
+    pano_status st;
+    if ((st = check_image(L, "L")) != PANO_OK) return st;
+    if ((st = check_image(R, "R")) != PANO_OK) return st;
+    if ((st = check_image(F, "F")) != PANO_OK) return st;
+    if ((st = check_same(L, R, "L", "R")) != PANO_OK) return st;
+    if ((st = check_same(L, F, "L", "F")) != PANO_OK) return st;
+    const int h = L->h, w = L->w;
+    if (!label || label_pitch < (size_t)w) return fail(PANO_ERR_INVALID_ARG, "label is NULL or its pitch < w");
+    if (!blend || ((uintptr_t)blend) % 4 || blend_pitch < w)
+        return fail(PANO_ERR_INVALID_ARG, "blend is NULL, not 4-byte aligned or its pitch < w");
+    if (flow_h < 1 || flow_w < 1 || flow_y0 < 0 || flow_x0 < 0 || flow_h > h - flow_y0 || flow_w > w - flow_x0)
+        return fail(PANO_ERR_INVALID_ARG, "flow crop %dx%d at (%d, %d) is not inside the %dx%d canvas", flow_h,
+                    flow_w, flow_y0, flow_x0, h, w);
+    if ((st = check_flow(flow_LtoR, "flow_LtoR")) != PANO_OK) return st;
+    if ((st = check_flow(flow_RtoL, "flow_RtoL")) != PANO_OK) return st;
+    const size_t fb = (size_t)F->h * F->pitch_bytes, nflow = (size_t)flow_h * flow_w * 8;
+    if (overlaps(F->data, fb, L->data, (size_t)L->h * L->pitch_bytes) ||
+        overlaps(F->data, fb, R->data, (size_t)R->h * R->pitch_bytes) ||
+        overlaps(F->data, fb, label, (size_t)h * label_pitch) ||
+        overlaps(F->data, fb, blend, (size_t)h * blend_pitch * sizeof(float)) ||
+        overlaps(F->data, fb, flow_LtoR, nflow) || overlaps(F->data, fb, flow_RtoL, nflow))
+        return fail(PANO_ERR_INVALID_ARG, "F overlaps an input");
+    ComposeArgs a;
+    a.L = desc(L);
+    a.R = desc(R);
+    a.label = label;
+    a.label_pitch = (long long)label_pitch;
+    a.blend = blend;
+    a.blend_pitch = blend_pitch;
+    a.flowLR = reinterpret_cast<const float2*>(flow_LtoR);
+    a.flowRL = reinterpret_cast<const float2*>(flow_RtoL);
+    a.fy0 = flow_y0;
+    a.fx0 = flow_x0;
+    a.fh = flow_h;
+    a.fw = flow_w;
+    a.F = F->data;
+    a.F_pitch_bytes = (long long)F->pitch_bytes;
+    a.k_sharp = p->soft_sharpness;
+    a.k_mag = p->flow_mag_coef;
+    a.inv_fw = 1.0f / (float)flow_w;
+    NvtxRange range("pano_compose_pair");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = launch_compose(a, s);
+    if (e != cudaSuccess) return cuda_fail(e, "compose launch");
+    if ((e = debug_check(s)) != cudaSuccess) return cuda_fail(e, "compose (PANO_DEBUG=sync)");
+    return PANO_OK;
+}
+
 pano_status pano_trace_enable(pano_flow_ctx* c, unsigned kind_mask, int capacity) {
     if (!c) return fail(PANO_ERR_INVALID_ARG, "context is NULL");
     return trace_enable(c->tr, kind_mask, capacity);

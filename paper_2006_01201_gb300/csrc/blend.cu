@@ -1,6 +1,7 @@
 // blend.cu -- the asymmetric softmax blend of Code 1 (Section III-C-3) with
-// the global blending coefficient of Eq. (1) (Section III-C-2), and the plain
-// bilinear flow warp.
+// the global blending coefficient of Eq. (1) (Section III-C-2): on overlap
+// strips, on a rig's canvas and on a whole canvas with every branch of
+// Code 1; and the plain bilinear flow warp.
 //
 // Code 1, Area3 branch, at pixel p = (x, y) of the overlap strips:
 //   BlendL = 1 - Blend(p), BlendR = Blend(p)
@@ -40,28 +41,24 @@ __device__ __forceinline__ float sample_channel(const Tv* __restrict__ base, con
                         sample_f(base[t.o11 + k]));
 }
 
-// F at strip pixel (x, y), stored at column `fx` of row y of a.F.
+// Code 1, Area3 branch, at pixel (x, y) of images L, R (h x w, row pitches
+// in elements): Blend B, flows rl = FlowRtoL(p) and lr = FlowLtoR(p),
+// inv_w = 1 / (width of the overlap strip); C channels to out.
 template <typename Tv, int C>
-__device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y, int fx) {
-    const int w = a.L.w, h = a.L.h;
-    const long long p = (long long)y * w + x;
-    const float B = a.blend ? a.blend[p] : (float)(x + 1) * a.inv_w1;
-    const float2 rl = a.flowRL[p], lr = a.flowLR[p];
+__device__ __forceinline__ void code1_area3(const Tv* __restrict__ Lb, int pitchL, const Tv* __restrict__ Rb,
+                                            int pitchR, int w, int h, int x, int y, float B, float2 rl,
+                                            float2 lr, float inv_w, float k_sharp, float k_mag, Tv* out) {
     const float blendL = 1.f - B, blendR = B;
     // ColorL at p + (1 - BlendL) FlowRtoL, ColorR at p + (1 - BlendR) FlowLtoR
-    const int pitchL = (int)(a.L.pitch_bytes / sizeof(Tv)), pitchR = (int)(a.R.pitch_bytes / sizeof(Tv));
     const Taps tl = bilinear_taps(x, y, (1.f - blendL) * rl.x, (1.f - blendL) * rl.y, w, h, pitchL, C);
     const Taps tr = bilinear_taps(x, y, (1.f - blendR) * lr.x, (1.f - blendR) * lr.y, w, h, pitchR, C);
-    const float magRL = sqrtf(fmaf(rl.x, rl.x, rl.y * rl.y)) * a.inv_w;
-    const float magLR = sqrtf(fmaf(lr.x, lr.x, lr.y * lr.y)) * a.inv_w;
-    const float sL = a.k_sharp * blendL * fmaf(a.k_mag, magRL, 1.f);
-    const float sR = a.k_sharp * blendR * fmaf(a.k_mag, magLR, 1.f);
+    const float magRL = sqrtf(fmaf(rl.x, rl.x, rl.y * rl.y)) * inv_w;
+    const float magLR = sqrtf(fmaf(lr.x, lr.x, lr.y * lr.y)) * inv_w;
+    const float sL = k_sharp * blendL * fmaf(k_mag, magRL, 1.f);
+    const float sR = k_sharp * blendR * fmaf(k_mag, magLR, 1.f);
     const float e = expf(fminf(fmaxf(sR - sL, -80.f), 80.f));
     const float wL = 1.f / (1.f + e);
     const float wR = e * wL;
-    const Tv* __restrict__ Lb = static_cast<const Tv*>(a.L.data);
-    const Tv* __restrict__ Rb = static_cast<const Tv*>(a.R.data);
-    Tv* out = reinterpret_cast<Tv*>(static_cast<char*>(a.F) + (long long)y * a.F_pitch_bytes) + (long long)fx * C;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
         const float cl = sample_channel(Lb, tl, k);
@@ -73,6 +70,18 @@ __device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y, in
             out[k] = (Tv)f;
         }
     }
+}
+
+// F at strip pixel (x, y), stored at column `fx` of row y of a.F.
+template <typename Tv, int C>
+__device__ __forceinline__ void blend_pixel(const BlendArgs& a, int x, int y, int fx) {
+    const int w = a.L.w, h = a.L.h;
+    const long long p = (long long)y * w + x;
+    const float B = a.blend ? a.blend[p] : (float)(x + 1) * a.inv_w1;
+    const int pitchL = (int)(a.L.pitch_bytes / sizeof(Tv)), pitchR = (int)(a.R.pitch_bytes / sizeof(Tv));
+    Tv* out = reinterpret_cast<Tv*>(static_cast<char*>(a.F) + (long long)y * a.F_pitch_bytes) + (long long)fx * C;
+    code1_area3<Tv, C>(static_cast<const Tv*>(a.L.data), pitchL, static_cast<const Tv*>(a.R.data), pitchR, w, h,
+                       x, y, B, a.flowRL[p], a.flowLR[p], a.inv_w, a.k_sharp, a.k_mag, out);
 }
 
 template <typename Tv, int C>
@@ -104,6 +113,40 @@ __global__ void __launch_bounds__(256, 8) rig_blend_kernel(const __grid_constant
         if (d < r.pair[q].L.w) return;
     }
     blend_pixel<Tv, C>(a, x, y, cx);
+}
+
+// Code 1 on a whole canvas, every branch: Area1 (label 1) copies L, Area2
+// (label 2) copies R, Area3 (label 3) blends with the flows of the overlap
+// crop (zero outside it), any other label writes 0.
+template <typename Tv, int C>
+__global__ void __launch_bounds__(256, 8) compose_kernel(ComposeArgs a) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    const int w = a.L.w, h = a.L.h;
+    if (x >= w || y >= h) return;
+    const int pitchL = (int)(a.L.pitch_bytes / sizeof(Tv)), pitchR = (int)(a.R.pitch_bytes / sizeof(Tv));
+    const Tv* __restrict__ Lb = static_cast<const Tv*>(a.L.data);
+    const Tv* __restrict__ Rb = static_cast<const Tv*>(a.R.data);
+    Tv* out = reinterpret_cast<Tv*>(static_cast<char*>(a.F) + (long long)y * a.F_pitch_bytes) + (long long)x * C;
+    const unsigned char area = a.label[(long long)y * a.label_pitch + x];
+    if (area == 1 || area == 2) {
+        const Tv* src = (area == 1 ? Lb + (long long)y * pitchL : Rb + (long long)y * pitchR) + (long long)x * C;
+#pragma unroll
+        for (int k = 0; k < C; ++k) out[k] = src[k];
+    } else if (area == 3) {
+        float2 rl = make_float2(0.f, 0.f), lr = make_float2(0.f, 0.f);
+        const int qy = y - a.fy0, qx = x - a.fx0;
+        if ((unsigned)qy < (unsigned)a.fh && (unsigned)qx < (unsigned)a.fw) {
+            const long long q = (long long)qy * a.fw + qx;
+            rl = a.flowRL[q];
+            lr = a.flowLR[q];
+        }
+        code1_area3<Tv, C>(Lb, pitchL, Rb, pitchR, w, h, x, y, a.blend[(long long)y * a.blend_pitch + x], rl, lr,
+                           a.inv_fw, a.k_sharp, a.k_mag, out);
+    } else {
+#pragma unroll
+        for (int k = 0; k < C; ++k) out[k] = (Tv)0;
+    }
 }
 
 template <typename Tv>
@@ -156,6 +199,19 @@ cudaError_t launch_rig_blend(const RigBlendArgs& args, cudaStream_t s) {
     } else {
         if (d.c == 3) rig_blend_kernel<float, 3><<<grid, block, 0, s>>>(r);
         else rig_blend_kernel<float, 1><<<grid, block, 0, s>>>(r);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_compose(const ComposeArgs& a, cudaStream_t s) {
+    dim3 block(32, 8);
+    dim3 grid((a.L.w + 31) / 32, (a.L.h + 7) / 8);
+    if (a.L.dtype == 0) {
+        if (a.L.c == 3) compose_kernel<uint8_t, 3><<<grid, block, 0, s>>>(a);
+        else compose_kernel<uint8_t, 1><<<grid, block, 0, s>>>(a);
+    } else {
+        if (a.L.c == 3) compose_kernel<float, 3><<<grid, block, 0, s>>>(a);
+        else compose_kernel<float, 1><<<grid, block, 0, s>>>(a);
     }
     return cudaGetLastError();
 }

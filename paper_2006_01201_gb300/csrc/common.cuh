@@ -204,6 +204,22 @@ struct RigBlendArgs {
     int canvas_w;
 };
 
+// Code 1 on a whole canvas (every branch).
+struct ComposeArgs {
+    ImageDesc L, R;                 // canvas images (same h, w, c, dtype)
+    const unsigned char* label;     // (h, w): 1 Area1, 2 Area2, 3 Area3, else neither
+    long long label_pitch;          // bytes
+    const float* blend;             // (h, w) Eq. (1)
+    int blend_pitch;                // floats
+    const float2* flowLR;           // (fh, fw) flows of the overlap crop
+    const float2* flowRL;
+    int fy0, fx0, fh, fw;           // canvas position and size of the crop
+    void* F;
+    long long F_pitch_bytes;
+    float k_sharp, k_mag;
+    float inv_fw;                   // 1 / fw, rounded to nearest
+};
+
 struct WarpArgs {
     ImageDesc src;
     const float2* flow;
@@ -260,6 +276,7 @@ cudaError_t lk_prepare(int max_smem_bytes);
 cudaError_t launch_blend(const BlendArgs& a, cudaStream_t s);
 cudaError_t launch_rig_blend(const RigBlendArgs& r, cudaStream_t s);
 cudaError_t launch_warp(const WarpArgs& a, cudaStream_t s);
+cudaError_t launch_compose(const ComposeArgs& a, cudaStream_t s);
 
 // Eq. (1) on a labelled canvas through an exact distance transform (edt.cu).
 size_t blend_coeff_scratch_bytes(int h, int w);

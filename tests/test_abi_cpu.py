@@ -109,6 +109,35 @@ def test_calls_reject_null_and_bad_images(lib):
                                     binding.PANO_LK_STREAM, None) == binding.PANO_ERR_UNSUPPORTED
 
 
+def test_compose_pair_rejects_bad_arguments_before_any_launch():
+    lib = binding.load_library()
+    par = binding.Params().to_c()
+    im = binding.PanoImage(0x10000, 8, 8, 3, 24, binding.PANO_U8)
+    out = binding.PanoImage(0x90000, 8, 8, 3, 24, binding.PANO_U8)
+    small = binding.PanoImage(0x20000, 8, 7, 3, 24, binding.PANO_U8)
+    inv, ok_args = binding.PANO_ERR_INVALID_ARG, dict(label=0x30000, lp=8, blend=0x40000, bp=8,
+                                                     lr=0x50000, rl=0x60000, y0=0, x0=2, fh=8, fw=4)
+
+    def call(L=im, R=im, F=out, **kw):
+        a = dict(ok_args, **kw)
+        return lib.pano_compose_pair(ctypes.byref(par), ctypes.byref(L), ctypes.byref(R), a["label"], a["lp"],
+                                     a["blend"], a["bp"], a["lr"], a["rl"], a["y0"], a["x0"], a["fh"], a["fw"],
+                                     ctypes.byref(F), None)
+
+    assert call(R=small) == inv                      # canvas sizes differ
+    assert call(label=None) == inv
+    assert call(lp=7) == inv                         # label pitch < w
+    assert call(blend=0x40002) == inv                # misaligned Blend
+    assert call(x0=5) == inv                         # crop leaves the canvas (5 + 4 > 8)
+    assert call(fh=0) == inv                         # empty crop
+    assert call(y0=-1) == inv
+    assert call(lr=0x50004) == inv                   # flow not 8-byte aligned
+    assert call(F=binding.PanoImage(0x10000, 8, 8, 3, 24, binding.PANO_U8)) == inv   # F is L
+    assert b"overlaps" in lib.pano_last_error(None)
+    assert lib.pano_compose_pair(None, ctypes.byref(im), ctypes.byref(im), 0x30000, 8, 0x40000, 8, 0x50000,
+                                 0x60000, 0, 0, 8, 8, ctypes.byref(out), None) == inv
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(binding.PanoError):
