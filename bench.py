@@ -291,7 +291,7 @@ def oracle_baseline(pair, levels: int, budget_s: float, label: str):
 
 # The paper's own figure (whole workflow, one 9000x4000 panorama, GPU model
 # not stated): context for the rig numbers, not a target.
-PAPER_CONTEXT = "under 30 s per 9000x4000 panorama for the whole workflow on an unspecified GPU (Sections I and V)"
+PAPER_CONTEXT = "under 30 s per 9000x4000 panorama for the whole workflow on an unspecified GPU (abstract, Section IV)"
 
 # FP32 arithmetic of one LK step per level pixel: bilinear sample 8, It 1,
 # products 2, separable box sums 8, 2x2 solve 12, update 2, plus gradient
@@ -517,7 +517,7 @@ def run_gpu(args):
                          / fp32_peak_tflops(clocks["sm_mhz"] if clocks else 2070.0),
                          "flops_per_step": path_flops},
                 "kernels": per_kind, "dominant_kernel": dominant,
-                "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks, "paper_context": PAPER_CONTEXT,
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
         if world == 1 and not args.no_cpu_baseline:
             import oracle
