@@ -272,6 +272,20 @@ class FlowContext:
         lr, rl = self.flow_pair(L, R, stream=stream)
         return lr, rl, self.blend_pair(L, R, lr, rl, stream=stream)
 
+    def stitch_canvas(self, L, R, label, crop, blend=None, out=None, stream=None):
+        """Section III-C on a canvas, in the paper's order: Blend of Eq. (1) on
+        the label canvas (pano_blend_coeff, unless `blend` is given), the flows
+        of the overlap crop (pano_flow_pair on the crop of L and R), and
+        Code 1 on the whole canvas (pano_compose_pair). crop = (row, column,
+        height, width) of the overlap on the canvas, within the context's
+        maxima. Returns (FlowLtoR, FlowRtoL, Blend, F)."""
+        y0, x0, ch, cw = (int(v) for v in crop)
+        if blend is None:
+            blend = blend_coeff(label, stream=stream)
+        lr, rl = self.flow_pair(L[y0:y0 + ch, x0:x0 + cw], R[y0:y0 + ch, x0:x0 + cw], stream=stream)
+        F = compose_pair(L, R, label, blend, lr, rl, origin=(y0, x0), params=self.params, out=out, stream=stream)
+        return lr, rl, blend, F
+
     def stitch_host(self, L_host, R_host, F_host, work, stream=None):
         """Whole path from host strips to a host F on one stream.
 

@@ -142,6 +142,27 @@ def test_compose_bad_arguments_raise():
         binding.compose_pair(L, L, lab, B, f, f, out=L)                # F is an input
 
 
+def test_stitch_canvas_runs_eq1_flow_and_code1_in_order():
+    # a synthetic overlap pair with Area1 / Area2 margins around it
+    pair = synth.pair_fullres_rgb(seed=4, h=160, w=240, dmax=8.0, levels=4)
+    h, ws = pair.shape
+    m = 40
+    L = np.concatenate([_image(h, m, 3, np.uint8, 13), pair.L, pair.L[:, -m:]], 1)
+    R = np.concatenate([pair.R[:, :m], pair.R, _image(h, m, 3, np.uint8, 14)], 1)
+    lab = np.full((h, ws + 2 * m), 3, np.uint8)
+    lab[:, :m], lab[:, m + ws:] = 1, 2
+    p = binding.Params(levels=4)
+    with binding.FlowContext(p, max_h=h, max_w=ws, max_c=3) as ctx:
+        lr, rl, B, F = ctx.stitch_canvas(cuda(L), cuda(R), cuda(lab), (0, m, h, ws))
+    lr, rl, B, F = host(lr), host(rl), host(B), host(F)
+    np.testing.assert_allclose(B, oracle.blend_coeff(lab), rtol=0, atol=1e-6)
+    olr, orl = oracle.flow_pair(L[:, m:m + ws], R[:, m:m + ws], oracle.Params(levels=4))
+    assert np.hypot(*(lr - olr).transpose(2, 0, 1)).mean() <= 0.05
+    assert np.hypot(*(rl - orl).transpose(2, 0, 1)).mean() <= 0.05
+    Fo = oracle.compose(L, R, lab, B.astype(np.float64), lr, rl, (0, m), oracle.Params(levels=4))
+    _check(F, Fo, lab, np.uint8)
+
+
 @pytest.mark.slow
 def test_full_size_canvas_around_the_benchmark_pair():
     """4000 x 3000 RGB u8 canvas: Area1 | the 4000 x 1500 overlap of the
