@@ -74,6 +74,27 @@ def test_repeated_static_calls_give_the_same_flow():
     assert torch.equal(b[0], a[1]) and torch.equal(b[1], a[0])
 
 
+def test_largest_strip_that_fits_runs_and_one_more_column_is_refused():
+    # 1024 x 1024 with 4 levels needs 16.65 MB of the 16 MiB scratch; a
+    # 1025th column rounds every level's row pitch up by 32 floats (17.37 MB)
+    g = np.random.default_rng(5)
+    from scipy import ndimage
+    T = ndimage.gaussian_filter(g.uniform(0, 1, (1024, 1025)), 1.5).astype(np.float32)
+    J = np.roll(T, (1, 2), axis=(0, 1))
+    params = binding.Params(levels=4)
+    L = torch.from_numpy(np.ascontiguousarray(T[:, :1024])).to(DEV)
+    R = torch.from_numpy(np.ascontiguousarray(J[:, :1024])).to(DEV)
+    s_lr, s_rl = binding.flow_pair_static(params, L, R)
+    with binding.FlowContext(params, max_h=1024, max_w=1024, max_c=1) as ctx:
+        c_lr, c_rl = ctx.flow_pair(L, R)
+        torch.cuda.synchronize()
+    assert (s_lr - c_lr).abs().max().item() <= MAX_ABS and (s_rl - c_rl).abs().max().item() <= MAX_ABS
+    wide = torch.from_numpy(T).to(DEV)
+    with pytest.raises(binding.PanoError) as ei:
+        binding.flow_pair_static(params, wide, wide)
+    assert ei.value.status == binding.PANO_ERR_INVALID_ARG and "scratch" in ei.value.message
+
+
 def test_strip_too_large_for_the_fixed_scratch_is_refused():
     big = torch.zeros((2048, 2048), dtype=torch.float32, device=DEV)
     with pytest.raises(binding.PanoError) as ei:
