@@ -373,6 +373,18 @@ PANO_API pano_status pano_stage_lk_kernel(const float* T, const float* J, int h,
 PANO_API pano_status pano_stage_warp(const pano_image* src, const float* flow, float scale,
                             pano_image* dst, void* cuda_stream);
 
+/* ----------------------------------------------------------------------
+ * Index checks (debug build only). The `check` variant of the library
+ * (build.build(variant="check"), compiled with -DPANO_BOUNDS_CHECK) checks
+ * every shared-memory index and every global index of the two LK kernels
+ * before the access. An index outside its array is counted, the first one
+ * recorded, and the access clamped into the array, so nothing traps.
+ * pano_debug_bounds copies the record into out[4] = {count, site, index,
+ * bound} and clears it; call it after the work has completed (synchronise
+ * first). In the normal build it writes zeros and returns UNSUPPORTED.
+ * Errors: INVALID_ARG (out NULL), UNSUPPORTED, CUDA. */
+PANO_API pano_status pano_debug_bounds(unsigned* out);
+
 #ifdef __cplusplus
 }
 #endif

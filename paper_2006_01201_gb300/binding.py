@@ -77,6 +77,7 @@ SIGNATURES = {
     "pano_flow_create": ([_PAR, _I, _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
     "pano_flow_pair": ([_VP, _IMG, _IMG, _VP, _VP, _VP], _I),
     "pano_blend_pair": ([_VP, _IMG, _IMG, _VP, _VP, _VP, _IMG, _VP], _I),
+    "pano_debug_bounds": ([ctypes.POINTER(ctypes.c_uint)], _I),
     "pano_compose_pair": ([_PAR, _IMG, _IMG, _VP, ctypes.c_size_t, _VP, _I, _VP, _VP, _I, _I, _I, _I, _IMG, _VP], _I),
     "pano_flow_destroy": ([_VP], _I),
     "pano_last_error": ([_VP], ctypes.c_char_p),
@@ -120,11 +121,9 @@ class PanoError(RuntimeError):
         self.message = message
 
 
-def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
-    """Load the CUDA library (build it first with ``build.build()``)."""
-    global _lib
-    if _lib is not None:
-        return _lib
+def open_library(path: str) -> ctypes.CDLL:
+    """A library file of this project (the release or the check variant) with
+    every C-ABI signature set; does not make it the one the binding uses."""
     if not os.path.exists(path):
         raise PanoError(-1, f"CUDA library not built: {path} is missing "
                             "(run paper_2006_01201_gb300.build.build())")
@@ -133,8 +132,24 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         f = getattr(lib, name)
         f.argtypes = args
         f.restype = res
-    _lib = lib
     return lib
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the CUDA library (build it first with ``build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    _lib = open_library(path)
+    return _lib
+
+
+def debug_bounds():
+    """(count, site, index, bound) of the index checks of the check variant
+    since the last read (pano_debug_bounds); synchronise before calling."""
+    out = (ctypes.c_uint * 4)()
+    _check(load_library().pano_debug_bounds(out))
+    return tuple(out)
 
 
 def _check(status: int) -> None:

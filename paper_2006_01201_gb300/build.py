@@ -3,6 +3,10 @@
 Each ``csrc/*.cu`` is compiled by nvcc in parallel, then linked with
 ``nvcc -shared``. Only one target is generated:
 ``-gencode arch=compute_103a,code=sm_103a`` (GB300).
+
+``build(variant="check")`` builds the debug library
+``_build_check/libpanoflow_check.so`` with the index checks of the LK
+kernels compiled in (``-DPANO_BOUNDS_CHECK``; see ``pano_debug_bounds``).
 """
 from __future__ import annotations
 
@@ -18,6 +22,11 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpanoflow.so")
+VARIANTS = {  # name: (build folder, library, extra nvcc flags)
+    "release": (BUILD, LIB, []),
+    "check": (os.path.join(HERE, "_build_check"), os.path.join(HERE, "_build_check", "libpanoflow_check.so"),
+              ["-DPANO_BOUNDS_CHECK"]),
+}
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -36,26 +45,28 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     deps = (sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + glob.glob(os.path.join(CSRC, "*.h"))
             + glob.glob(os.path.join(INCLUDE, "*.h")))
     deps.append(os.path.abspath(__file__))
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile and link the library if any source is newer than it."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False, variant: str = "release") -> str:
+    """Compile and link the library (or its `check` variant) if any source is
+    newer than it; returns its path."""
+    build_dir, lib, flags = VARIANTS[variant]
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(build_dir, exist_ok=True)
     nvcc = _nvcc()
-    extra = ["-Xptxas", "-v"] if ptxas_info else []
+    extra = (["-Xptxas", "-v"] if ptxas_info else []) + flags
 
     def compile_one(src):
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
+        obj = os.path.join(build_dir, os.path.basename(src).replace(".cu", ".o"))
         cmd = [nvcc, *ARCH, *FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -66,14 +77,14 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
 
     with ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 1)) as ex:
         objs = list(ex.map(compile_one, sources()))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     # --no-undefined: a missing definition fails the build, not the first load
     cmd = [nvcc, *ARCH, "-shared", "-Xcompiler", "-fPIC", "-Xlinker", "--no-undefined", *objs, "-o", tmp]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

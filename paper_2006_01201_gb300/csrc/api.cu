@@ -638,6 +638,20 @@ pano_status pano_compose_pair(const pano_flow_params* p, const pano_image* L, co
     return PANO_OK;
 }
 
+pano_status pano_debug_bounds(unsigned* out) {
+    if (!out) return fail(PANO_ERR_INVALID_ARG, "out is NULL");
+    out[0] = out[1] = out[2] = out[3] = 0;
+#ifdef PANO_BOUNDS_CHECK
+    cudaError_t e;
+    if ((e = bounds_read_lk_stream(out)) != cudaSuccess || (e = bounds_read_lk_stream_bf16(out)) != cudaSuccess ||
+        (e = bounds_read_lk_stream_f16(out)) != cudaSuccess || (e = bounds_read_lk_tile(out)) != cudaSuccess)
+        return cuda_fail(e, "reading the index-check records");
+    return PANO_OK;
+#else
+    return fail(PANO_ERR_UNSUPPORTED, "this build has no index checks (build the check variant)");
+#endif
+}
+
 pano_status pano_trace_enable(pano_flow_ctx* c, unsigned kind_mask, int capacity) {
     if (!c) return fail(PANO_ERR_INVALID_ARG, "context is NULL");
     return trace_enable(c->tr, kind_mask, capacity);

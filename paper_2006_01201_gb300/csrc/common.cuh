@@ -289,6 +289,14 @@ cudaError_t launch_energy_grad(const EnergyArgs& a, cudaStream_t s);
 cudaError_t launch_pyr_down_adjoint(const float* gdst, int h, int w, int dst_pitch, float* gsrc, int src_pitch,
                                     cudaStream_t s);
 
+// Index-check records of the debug build (bounds.cuh), one per translation
+// unit: each adds its record to out[4] and clears it (no-ops in the normal
+// build).
+cudaError_t bounds_read_lk_stream(unsigned* out);
+cudaError_t bounds_read_lk_stream_bf16(unsigned* out);
+cudaError_t bounds_read_lk_stream_f16(unsigned* out);
+cudaError_t bounds_read_lk_tile(unsigned* out);
+
 // Stores the message that pano_last_error() returns on the calling thread.
 void set_last_error(const char* msg);
 

@@ -23,6 +23,7 @@
 // the kernel works with flows relative to one reference flow per tile (the
 // starting flow at the tile centre); the equations above are unchanged by
 // that shift.
+#include "bounds.cuh"
 #include "common.cuh"
 
 namespace pano {
@@ -53,8 +54,9 @@ __device__ __forceinline__ float sample_box(const float* __restrict__ sJ, int jb
         Taps t;
         t.ax = cx - fx;
         t.ay = cy - fy;
-        const float* r0 = sJ + by * jbw + bx;
-        return bilinear_mix(t, r0[0], r0[1], r0[jbw], r0[jbw + 1]);
+        const int o = by * jbw + bx, nj = jbw * jbh;
+        return bilinear_mix(t, PANO_AT(sJ, o, nj, 201), PANO_AT(sJ, o + 1, nj, 202), PANO_AT(sJ, o + jbw, nj, 203),
+                            PANO_AT(sJ, o + jbw + 1, nj, 204));
     }
     return sample_plane(J, pitchJ, w, h, qx, qy, ox, oy);
 }
@@ -114,9 +116,9 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
                 u = start_flow(a, D, x, y);
             }
             const int i = ry * RW + rx;
-            sT[i] = t;
-            sG[i] = g;
-            sU[i] = u;
+            PANO_AT(sT, i, N, 205) = t;
+            PANO_AT(sG, i, N, 206) = g;
+            PANO_AT(sU, i, N, 207) = u;
         }
     }
     __syncthreads();
@@ -124,7 +126,7 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
     // Reference flow: the starting flow at the tile centre (inside the image).
     const int cx = min(bx * a.tile_w + a.tile_w / 2, w - 1);
     const int cy = min(by * a.tile_h + a.tile_h / 2, h - 1);
-    const float2 ref = sU[(cy - oy) * RW + (cx - ox)];
+    const float2 ref = PANO_AT(sU, (cy - oy) * RW + (cx - ox), N, 208);
 
     // the staged target box (clamped values), shifted by the reference flow
     const int jbw = tile_jbw(RW), jbh = tile_jbh(RH);
@@ -136,28 +138,28 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
         for (int i = threadIdx.x; i < jbw * jbh; i += blockDim.x) {
             const int r = i / jbw, c = i - r * jbw;
             const int yy = min(max(jy0 + r, 0), h - 1), xx = min(max(jx0 + c, 0), w - 1);
-            sJ[i] = ld_f32(J + (long long)yy * pitchJ + xx);
+            PANO_AT(sJ, i, jbw * jbh, 209) = ld_f32(&PANO_AT(J, (long long)yy * pitchJ + xx, (long long)h * pitchJ, 210));
         }
         // Relative flows and the inverse normal matrices on R_1 (margin RAD).
         for (int ry = warp; ry < RH; ry += nwarps) {
             for (int rx = lane; rx < RW; rx += 32) {
                 const int i = ry * RW + rx;
-                float2 u = sU[i];
-                sU[i] = make_float2(u.x - ref.x, u.y - ref.y);
+                float2 u = PANO_AT(sU, i, N, 211);
+                PANO_AT(sU, i, N, 211) = make_float2(u.x - ref.x, u.y - ref.y);
                 if (ry < RAD || ry >= RH - RAD || rx < RAD || rx >= RW - RAD) continue;
                 float g11 = 0.f, g12 = 0.f, g22 = 0.f;
 #pragma unroll
                 for (int dy = -RAD; dy <= RAD; ++dy)
 #pragma unroll
                     for (int dx = -RAD; dx <= RAD; ++dx) {
-                        float2 g = sG[i + dy * RW + dx];
+                        float2 g = PANO_AT(sG, i + dy * RW + dx, N, 212);
                         g11 = fmaf(g.x, g.x, g11);
                         g12 = fmaf(g.x, g.y, g12);
                         g22 = fmaf(g.y, g.y, g22);
                     }
                 const float a11 = g11 + a.lambda, a22 = g22 + a.lambda;
                 const float inv = 1.0f / (a11 * a22 - g12 * g12);
-                sGi[i] = make_float4(a22 * inv, -g12 * inv, a11 * inv, 0.f);
+                PANO_AT(sGi, i, N, 213) = make_float4(a22 * inv, -g12 * inv, a11 * inv, 0.f);
             }
         }
         __syncthreads();
@@ -172,15 +174,15 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
                     const int i = ry * RW + rx;
                     float2 P = make_float2(0.f, 0.f);
                     if (x >= 0 && x < w && y >= 0 && y < h) {
-                        const float2 u = sU[i];
-                        const float2 g = sG[i];
+                        const float2 u = PANO_AT(sU, i, N, 214);
+                        const float2 g = PANO_AT(sG, i, N, 215);
                         const float Jw = sample_box(sJ, jbw, jbh, jx0, jy0, J, pitchJ, w, h, x, y, ref.x + u.x,
                                                     ref.y + u.y);
-                        const float It = Jw - sT[i];
+                        const float It = Jw - PANO_AT(sT, i, N, 216);
                         const float s = fmaf(g.x, u.x, fmaf(g.y, u.y, -It));
                         P = make_float2(g.x * s, g.y * s);
                     }
-                    sP[i] = P;
+                    PANO_AT(sP, i, N, 217) = P;
                 }
             }
             __syncthreads();
@@ -188,14 +190,14 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
             for (int ry = mC + warp; ry < RH - mC; ry += nwarps) {
                 for (int rx = mA + lane; rx < RW - mA; rx += 32) {
                     const int i = ry * RW + rx;
-                    float2 v = sP[i - RAD * RW];
+                    float2 v = PANO_AT(sP, i - RAD * RW, N, 218);
 #pragma unroll
                     for (int dy = -RAD + 1; dy <= RAD; ++dy) {
-                        float2 q = sP[i + dy * RW];
+                        float2 q = PANO_AT(sP, i + dy * RW, N, 219);
                         v.x += q.x;
                         v.y += q.y;
                     }
-                    sV[i] = v;
+                    PANO_AT(sV, i, N, 220) = v;
                 }
             }
             __syncthreads();
@@ -206,17 +208,17 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
                     const int x = ox + rx;
                     if (x < 0 || x >= w || y < 0 || y >= h) continue;
                     const int i = ry * RW + rx;
-                    float2 m = sV[i - RAD];
+                    float2 m = PANO_AT(sV, i - RAD, N, 221);
 #pragma unroll
                     for (int dx = -RAD + 1; dx <= RAD; ++dx) {
-                        float2 q = sV[i + dx];
+                        float2 q = PANO_AT(sV, i + dx, N, 222);
                         m.x += q.x;
                         m.y += q.y;
                     }
-                    const float2 u = sU[i];
-                    const float4 gi = sGi[i];
+                    const float2 u = PANO_AT(sU, i, N, 223);
+                    const float4 gi = PANO_AT(sGi, i, N, 224);
                     const float r1 = fmaf(a.lambda, u.x, m.x), r2 = fmaf(a.lambda, u.y, m.y);
-                    sU[i] = make_float2(fmaf(gi.x, r1, gi.y * r2), fmaf(gi.y, r1, gi.z * r2));
+                    PANO_AT(sU, i, N, 225) = make_float2(fmaf(gi.x, r1, gi.y * r2), fmaf(gi.y, r1, gi.z * r2));
                 }
             }
             __syncthreads();
@@ -232,8 +234,9 @@ __device__ __forceinline__ void lk_tile_item(const LkArgs& a, int dir, int bx, i
         for (int tx = lane; tx < a.tile_w; tx += 32) {
             const int x = bx * a.tile_w + tx;
             if (x >= w) break;
-            const float2 u = sU[(ty + halo) * RW + (tx + halo)];
-            uo[(long long)y * D.uout_pitch + x] = make_float2(u.x + add.x, u.y + add.y);
+            const float2 u = PANO_AT(sU, (ty + halo) * RW + (tx + halo), N, 226);
+            PANO_AT(uo, (long long)y * D.uout_pitch + x, (long long)h * D.uout_pitch, 227) =
+                make_float2(u.x + add.x, u.y + add.y);
         }
     }
 }
@@ -336,6 +339,8 @@ cudaError_t launch_lk_level(const LkArgs& a, int ndirs, cudaStream_t s) {
         return launch_lk_stream(a, ndirs, s);
     return launch_lk_tile(a, ndirs, s);
 }
+
+PANO_BOUNDS_READER(bounds_read_lk_tile)
 
 cudaError_t launch_lk_tile_batch(const LkBatch& b, cudaStream_t s) {
     if (b.n < 1 || b.n > kMaxBatch) return cudaErrorInvalidValue;

@@ -12,6 +12,8 @@ PANO_LKS_EXTERN(__nv_bfloat16)
 PANO_LKS_EXTERN(__half)
 }  // namespace lks
 
+PANO_BOUNDS_READER(bounds_read_lk_stream)
+
 bool lk_stream_supports(int iters, int radius) { return iters >= 1 && iters <= 5 && radius >= 1 && radius <= 3; }
 
 cudaError_t lk_stream_prepare(int max_smem_bytes) {

@@ -6,4 +6,5 @@ namespace pano {
 namespace lks {
 PANO_LKS_INSTANTIATE(__nv_bfloat16)
 }  // namespace lks
+PANO_BOUNDS_READER(bounds_read_lk_stream_bf16)
 }  // namespace pano

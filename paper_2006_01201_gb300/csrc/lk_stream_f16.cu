@@ -6,4 +6,5 @@ namespace pano {
 namespace lks {
 PANO_LKS_INSTANTIATE(__half)
 }  // namespace lks
+PANO_BOUNDS_READER(bounds_read_lk_stream_f16)
 }  // namespace pano

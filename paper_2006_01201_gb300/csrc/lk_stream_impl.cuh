@@ -44,6 +44,7 @@
 
 #include <type_traits>
 
+#include "bounds.cuh"
 #include "common.cuh"
 
 namespace pano {
@@ -72,13 +73,18 @@ struct StreamGeom {
     static constexpr size_t kJ = kGiB + sizeof(float) * kRing * RW;
     static constexpr size_t kP = kJ + sizeof(float) * kRing * JW;
     static constexpr size_t kH = kP + sizeof(float2) * PR * RW;
-    static constexpr size_t kV = kH + sizeof(float2) * K * 2 * RAD * RW;
-    static constexpr size_t kCSA = kV + sizeof(float2) * CH * RW;
-    static constexpr size_t kCSB = kCSA + sizeof(float2) * CH * RW;
+    // sV, sCSA and sCSB are padded by kPad elements on both sides: the row
+    // sums of the column pair at a stage's edge read a window of up to
+    // kPad elements beyond the first or last column (values of pixels the
+    // stage does not update, never used), which then stays in the array
+    static constexpr int kPad = 4;
+    static constexpr size_t kV = kH + sizeof(float2) * K * 2 * RAD * RW + sizeof(float2) * kPad;
+    static constexpr size_t kCSA = kV + sizeof(float2) * (CH * RW + kPad) + sizeof(float2) * kPad;
+    static constexpr size_t kCSB = kCSA + sizeof(float2) * (CH * RW + kPad) + sizeof(float) * kPad;
     // next chunk's template rows (with a 1-pixel ring) and coarse flow rows
     static constexpr int TSW = RW + 2, TSH = CH + 2;
     static constexpr int FSW = RW / 2 + 3, FSH = CH / 2 + 3;
-    static constexpr size_t kTS = kCSB + sizeof(float) * CH * RW;
+    static constexpr size_t kTS = kCSB + sizeof(float) * (CH * RW + kPad);
     static constexpr size_t kFS = (kTS + sizeof(float) * TSH * TSW + 7) / 8 * 8;
     static constexpr size_t bytes = kFS + sizeof(float2) * FSH * FSW;
 };
@@ -139,9 +145,10 @@ __device__ __forceinline__ float sample_target(const TargetBox<Ts>& b, int x, in
         Taps t;
         t.ax = ox - fx;
         t.ay = oy - fy;
-        const float* r0 = b.sJ + ring_slot(y + iy) * JW + bcol;
-        const float* r1 = b.sJ + ring_slot(y + iy + 1) * JW + bcol;
-        return bilinear_mix(t, r0[0], r0[1], r1[0], r1[1]);
+        const int o0 = ring_slot(y + iy) * JW + bcol, o1 = ring_slot(y + iy + 1) * JW + bcol;
+        constexpr int NJ = kRing * JW;
+        return bilinear_mix(t, PANO_AT(b.sJ, o0, NJ, 101), PANO_AT(b.sJ, o0 + 1, NJ, 102), PANO_AT(b.sJ, o1, NJ, 103),
+                            PANO_AT(b.sJ, o1 + 1, NJ, 104));
     }
     // outside the staged box (large or non-finite offsets): clamped global taps
     return sample_plane(b.J, b.pitchJ, b.w, b.h, x, y, ox, oy);
@@ -170,17 +177,17 @@ __device__ __forceinline__ void column_sums(const float2* __restrict__ sP, float
     const int r0 = part * HC;
     float2 p[HC + 2 * RAD];
 #pragma unroll
-    for (int d = 0; d < HC + 2 * RAD; ++d) p[d] = sP[(r0 + d) * RW + rx];
+    for (int d = 0; d < HC + 2 * RAD; ++d) p[d] = PANO_AT(sP, (r0 + d) * RW + rx, (CH + 2 * RAD) * RW, 105);
 #pragma unroll
     for (int yy = 0; yy < HC; ++yy) {
         float2 v = p[yy];
 #pragma unroll
         for (int d = 1; d <= 2 * RAD; ++d) v = add2(v, p[yy + d]);
-        sV[(r0 + yy) * RW + rx] = v;
+        PANO_AT(sV, (r0 + yy) * RW + rx, CH * RW, 106) = v;
     }
     if (part == S - 1) {
 #pragma unroll
-        for (int d = 0; d < 2 * RAD; ++d) hist[d * RW + rx] = p[HC + d];
+        for (int d = 0; d < 2 * RAD; ++d) PANO_AT(hist, d * RW + rx, 2 * RAD * RW, 107) = p[HC + d];
     }
 }
 
@@ -215,6 +222,10 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
     float* sTS = reinterpret_cast<float*>(smem + Geo::kTS);      // staged template rows
     float2* sFS = reinterpret_cast<float2*>(smem + Geo::kFS);    // staged coarse flow rows
     constexpr int TSW = Geo::TSW, TSH = Geo::TSH, FSW = Geo::FSW, FSH = Geo::FSH;
+    // element counts of the shared arrays (for the debug build's index checks)
+    constexpr int NR = kRing * RW, NJ = kRing * JW, NP = (CH + 2 * RAD) * RW, NHIST = K * 2 * RAD * RW;
+    constexpr int NCH = CH * RW, NTS = TSH * TSW, NFS = FSH * FSW;
+    (void)NR, (void)NJ, (void)NP, (void)NHIST, (void)NCH, (void)NTS, (void)NFS;
 
     const LkDir D = dir ? a.dir[1] : a.dir[0];
     const int w = a.w, h = a.h;
@@ -253,15 +264,17 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
         for (int i = wi; i < TSH * TSW; i += nw) {
             const int r = i / TSW, cc = i - r * TSW;
             const int ys = min(max(a0n - 1 + r, 0), h - 1), xs = min(max(ox - 1 + cc, 0), w - 1);
-            if constexpr (kAsyncT) copy_async4(sTS + i, T + (long long)ys * pitchT + xs);
-            else sTS[i] = ld_f32(T + (long long)ys * pitchT + xs);
+            const Ts* src = &PANO_AT(T, (long long)ys * pitchT + xs, (long long)h * pitchT, 110);
+            if constexpr (kAsyncT) copy_async4(&PANO_AT(sTS, i, NTS, 111), src);
+            else PANO_AT(sTS, i, NTS, 111) = ld_f32(src);
         }
         if (stage_flow) {
             const int cy0 = a0n >> 1, cx0 = ox >> 1;
             for (int i = wi; i < FSH * FSW; i += nw) {
                 const int r = i / FSW, cc = i - r * FSW;
                 const int ys = min(max(cy0 + r, 0), a.in_h - 1), xs = min(max(cx0 + cc, 0), a.in_w - 1);
-                copy_async8(sFS + i, ucoarse + (long long)ys * D.uin_pitch + xs);
+                copy_async8(&PANO_AT(sFS, i, NFS, 112),
+                            &PANO_AT(ucoarse, (long long)ys * D.uin_pitch + xs, (long long)a.in_h * D.uin_pitch, 113));
             }
         }
         copy_async_commit();
@@ -273,11 +286,11 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
     // Rings start at zero: the column sums of the first chunk read ring rows
     // that no earlier chunk wrote (their results are discarded, but must
     // stay finite).
-    for (int i = tid; i < K * 2 * RAD * RW; i += kStreamThreads) sH[i] = make_float2(0.f, 0.f);
+    for (int i = tid; i < K * 2 * RAD * RW; i += kStreamThreads) PANO_AT(sH, i, NHIST, 114) = make_float2(0.f, 0.f);
     for (int i = tid; i < kRing * RW; i += kStreamThreads) {
-        sT[i] = 0.f;
-        sG[i] = make_float2(0.f, 0.f);
-        sU[i] = make_float2(0.f, 0.f);
+        PANO_AT(sT, i, NR, 115) = 0.f;
+        PANO_AT(sG, i, NR, 116) = make_float2(0.f, 0.f);
+        PANO_AT(sU, i, NR, 117) = make_float2(0.f, 0.f);
     }
     {
         // target rows of the first chunk
@@ -288,7 +301,8 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
             const int yy = i / JW, bc = i - yy * JW;
             const int yj = yb + yy;
             const int ys = min(max(yj, 0), h - 1), xs = min(max(jx0 + bc, 0), w - 1);
-            sJ[ring_slot(yj) * JW + bc] = ld_f32(box.J + (long long)ys * box.pitchJ + xs);
+            PANO_AT(sJ, ring_slot(yj) * JW + bc, NJ, 118) =
+                ld_f32(&PANO_AT(box.J, (long long)ys * box.pitchJ + xs, (long long)h * box.pitchJ, 119));
         }
     }
     copy_async_wait_all();
@@ -297,32 +311,32 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
     for (int c = c_first; c <= c_last; ++c) {
         const int a0 = Y0 + K * RAD + c * CH;  // newest rows [a0, a0 + CH)
         // ---- X_0: state of the new rows and the products of stage 1
-        for (int i = tid; i < 2 * RAD * RW; i += kStreamThreads) sP[i] = sH[i];
+        for (int i = tid; i < 2 * RAD * RW; i += kStreamThreads) PANO_AT(sP, i, NP, 120) = PANO_AT(sH, i, NHIST, 121);
         {
             const int y = a0 + ty;
             const bool row_in = y >= 0 && y < h;
             const int srow = ring_slot(y) * RW;
-            const float* tsr = sTS + (ty + 1) * TSW + 1;  // staged row of y, column of rx at [rx]
+            const int tso = (ty + 1) * TSW + 1;  // staged row of y: column rx at sTS[tso + rx]
             const int cy0 = a0 >> 1, cx0 = ox >> 1;
             const int fr0 = (y >> 1) - cy0;               // staged coarse row of y / 2
             const float fy = (y & 1) ? 0.5f : 0.f;
-            float2* prow = sP + (2 * RAD + ty) * RW;
+            const int pro = (2 * RAD + ty) * RW;  // this row's products at sP[pro + rx]
             for (int rx = tx; rx < RW; rx += TX) {
                 const int x = ox + rx;
                 float t = 0.f;
                 float2 g = make_float2(0.f, 0.f), u = make_float2(0.f, 0.f), P = make_float2(0.f, 0.f);
                 if (row_in && rx >= cmin && rx < cmax) {
-                    t = tsr[rx];
-                    g.x = 0.5f * (tsr[rx + 1] - tsr[rx - 1]);
-                    g.y = 0.5f * (tsr[rx + TSW] - tsr[rx - TSW]);
+                    t = PANO_AT(sTS, tso + rx, NTS, 122);
+                    g.x = 0.5f * (PANO_AT(sTS, tso + rx + 1, NTS, 123) - PANO_AT(sTS, tso + rx - 1, NTS, 124));
+                    g.y = 0.5f * (PANO_AT(sTS, tso + rx + TSW, NTS, 125) - PANO_AT(sTS, tso + rx - TSW, NTS, 126));
                     float2 u0;
                     if (stage_flow) {
                         // 2 * bilinear(u_coarse)(x/2, y/2) from the staged rows
                         const int fc0 = (x >> 1) - cx0;
                         const float fx = (x & 1) ? 0.5f : 0.f;
-                        const float2* f0 = sFS + fr0 * FSW + fc0;
-                        const float2* f1 = f0 + FSW;
-                        const float2 u00 = f0[0], u10 = f0[1], u01 = f1[0], u11 = f1[1];
+                        const int f0 = fr0 * FSW + fc0, f1 = f0 + FSW;
+                        const float2 u00 = PANO_AT(sFS, f0, NFS, 127), u10 = PANO_AT(sFS, f0 + 1, NFS, 128);
+                        const float2 u01 = PANO_AT(sFS, f1, NFS, 129), u11 = PANO_AT(sFS, f1 + 1, NFS, 130);
                         const float tx0 = fmaf(fx, u10.x - u00.x, u00.x), bx0 = fmaf(fx, u11.x - u01.x, u01.x);
                         const float ty0 = fmaf(fx, u10.y - u00.y, u00.y), by0 = fmaf(fx, u11.y - u01.y, u01.y);
                         u0 = make_float2(2.f * fmaf(fy, bx0 - tx0, tx0), 2.f * fmaf(fy, by0 - ty0, ty0));
@@ -332,10 +346,10 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                     u = make_float2(u0.x - ref.x, u0.y - ref.y);
                     P = residual_product<JW, Ts>(box, x, y, rx, ref, u, g, t);
                 }
-                sT[srow + rx] = t;
-                sG[srow + rx] = g;
-                sU[srow + rx] = u;
-                prow[rx] = P;
+                PANO_AT(sT, srow + rx, NR, 131) = t;
+                PANO_AT(sG, srow + rx, NR, 132) = g;
+                PANO_AT(sU, srow + rx, NR, 133) = u;
+                PANO_AT(sP, pro + rx, NP, 134) = P;
             }
         }
         __syncthreads();
@@ -356,7 +370,7 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
             const int yb = a0 - 2 * RAD + half * HC;   // first ring row of this half's windows
             float2 g[HC + 2 * RAD];
 #pragma unroll
-            for (int d = 0; d < HC + 2 * RAD; ++d) g[d] = sG[ring_slot(yb + d) * RW + rx];
+            for (int d = 0; d < HC + 2 * RAD; ++d) g[d] = PANO_AT(sG, ring_slot(yb + d) * RW + rx, NR, 135);
 #pragma unroll
             for (int yy = 0; yy < HC; ++yy) {
                 float2 c1 = make_float2(0.f, 0.f);  // (c11, c12)
@@ -367,8 +381,8 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                     c22 = fmaf(g[yy + d].y, g[yy + d].y, c22);
                 }
                 const int o = (half * HC + yy) * RW + rx;
-                sCSA[o] = c1;
-                sCSB[o] = c22;
+                PANO_AT(sCSA, o, NCH, 136) = c1;
+                PANO_AT(sCSB, o, NCH, 137) = c22;
             }
         }
         __syncthreads();
@@ -380,26 +394,30 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                 // first time: asynchronous copies, issued first so that they
                 // overlap this phase (no products are sampled in it)
                 const int yj = a0 + CH + box.fref_y + kMY + 1 + ty;
-                const Ts* jsrc = box.J + (long long)min(max(yj, 0), h - 1) * box.pitchJ;
+                const long long jso = (long long)min(max(yj, 0), h - 1) * box.pitchJ;  // source row
+                const long long NJG = (long long)h * box.pitchJ;
+                (void)NJG;
                 if constexpr (kAsyncT) {
-                    float* jdst = sJ + ring_slot(yj) * JW;
-                    for (int bc = tx; bc < JW; bc += TX) copy_async4(jdst + bc, jsrc + min(max(jx0 + bc, 0), w - 1));
+                    const int jdo = ring_slot(yj) * JW;
+                    for (int bc = tx; bc < JW; bc += TX)
+                        copy_async4(&PANO_AT(sJ, jdo + bc, NJ, 138),
+                                    &PANO_AT(box.J, jso + min(max(jx0 + bc, 0), w - 1), NJG, 139));
                     copy_async_commit();
                 } else {
 #pragma unroll
                     for (int q = 0; q < kJPT; ++q) {
                         const int bc = tx + q * TX;
-                        jnext[q] = bc < JW ? ld_f32(jsrc + min(max(jx0 + bc, 0), w - 1)) : 0.f;
+                        jnext[q] = bc < JW ? ld_f32(&PANO_AT(box.J, jso + min(max(jx0 + bc, 0), w - 1), NJG, 139)) : 0.f;
                     }
                 }
             }
             // ---- X_k: row sums, solve, update; products of stage k+1
             if (k < K) {
-                const float2* hk = sH + (size_t)k * 2 * RAD * RW;
+                const int hko = k * 2 * RAD * RW;  // this stage's history in sH
                 const int width = RW - 2 * c0;
                 for (int i = tid; i < 2 * RAD * width; i += kStreamThreads) {
                     const int yy = i / width, rx = c0 + (i - yy * width);
-                    sP[yy * RW + rx] = hk[yy * RW + rx];
+                    PANO_AT(sP, yy * RW + rx, NP, 140) = PANO_AT(sH, hko + yy * RW + rx, NHIST, 141);
                 }
             }
             {
@@ -416,11 +434,12 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                     const bool in0 = on0 && row_in && xp >= cmin && xp < cmax;
                     const bool in1 = on1 && row_in && xp + 1 >= cmin && xp + 1 < cmax;
                     // row sums of the column sums for both pixels
-                    const float4* vq = reinterpret_cast<const float4*>(sV + ty * RW + xp - HR);
+                    const int vqo = ty * RW + xp - HR;  // first column pair at sV[vqo]
                     float2 vv[2 * HR + 2];
 #pragma unroll
                     for (int q = 0; q < NPAIR; ++q) {
-                        const float4 t4 = vq[q];
+                        const float4 t4 = PANO_VEC(const float4, sV - Geo::kPad, vqo + 2 * q + Geo::kPad, 2,
+                                                   NCH + 2 * Geo::kPad, 142);
                         vv[2 * q] = make_float2(t4.x, t4.y);
                         vv[2 * q + 1] = make_float2(t4.z, t4.w);
                     }
@@ -433,16 +452,16 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                     float2 ga0, ga1;
                     float gb0, gb1;
                     if (k == 1) {
-                        const float2* ca = sCSA + ty * RW + xp;
-                        const float* cb = sCSB + ty * RW + xp;
+                        const int co = ty * RW + xp;  // column sums of column xp at sCSA[co], sCSB[co]
                         float2 a1 = make_float2(0.f, 0.f), b1 = make_float2(0.f, 0.f);  // (x11, x12)
                         float a22 = 0.f, b22 = 0.f;
 #pragma unroll
                         for (int d = -RAD; d <= RAD; ++d) {
-                            a1 = add2(a1, ca[d]);
-                            a22 += cb[d];
-                            b1 = add2(b1, ca[d + 1]);
-                            b22 += cb[d + 1];
+                            constexpr int NCP = NCH + 2 * Geo::kPad, PD = Geo::kPad;
+                            a1 = add2(a1, PANO_AT(sCSA - PD, co + d + PD, NCP, 143));
+                            a22 += PANO_AT(sCSB - PD, co + d + PD, NCP, 144);
+                            b1 = add2(b1, PANO_AT(sCSA - PD, co + d + 1 + PD, NCP, 145));
+                            b22 += PANO_AT(sCSB - PD, co + d + 1 + PD, NCP, 146);
                         }
                         const float a11 = a1.x, a12 = a1.y, b11 = b1.x, b12 = b1.y;
                         const float p11 = a11 + lam, p22 = a22 + lam;
@@ -453,17 +472,17 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                         gb0 = p11 * ip;
                         ga1 = make_float2(q22 * iq, -b12 * iq);
                         gb1 = q11 * iq;
-                        *reinterpret_cast<float4*>(sGiA + srow + xp) = make_float4(ga0.x, ga0.y, ga1.x, ga1.y);
-                        *reinterpret_cast<float2*>(sGiB + srow + xp) = make_float2(gb0, gb1);
+                        PANO_VEC(float4, sGiA, srow + xp, 2, NR, 147) = make_float4(ga0.x, ga0.y, ga1.x, ga1.y);
+                        PANO_VEC(float2, sGiB, srow + xp, 2, NR, 148) = make_float2(gb0, gb1);
                     } else {
-                        const float4 a4 = *reinterpret_cast<const float4*>(sGiA + srow + xp);
-                        const float2 b2 = *reinterpret_cast<const float2*>(sGiB + srow + xp);
+                        const float4 a4 = PANO_VEC(const float4, sGiA, srow + xp, 2, NR, 149);
+                        const float2 b2 = PANO_VEC(const float2, sGiB, srow + xp, 2, NR, 150);
                         ga0 = make_float2(a4.x, a4.y);
                         ga1 = make_float2(a4.z, a4.w);
                         gb0 = b2.x;
                         gb1 = b2.y;
                     }
-                    const float4 u4 = *reinterpret_cast<const float4*>(sU + srow + xp);
+                    const float4 u4 = PANO_VEC(const float4, sU, srow + xp, 2, NR, 151);
                     float2 v0 = make_float2(u4.x, u4.y), v1 = make_float2(u4.z, u4.w);
                     const float2 lam2 = make_float2(lam, lam);
                     if (in0) {
@@ -474,23 +493,25 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                         const float2 r = fma2(lam2, v1, m1);
                         v1 = fma2(ga1, make_float2(r.x, r.x), mul2(make_float2(ga1.y, gb1), make_float2(r.y, r.y)));
                     }
-                    *reinterpret_cast<float4*>(sU + srow + xp) = make_float4(v0.x, v0.y, v1.x, v1.y);
+                    PANO_VEC(float4, sU, srow + xp, 2, NR, 152) = make_float4(v0.x, v0.y, v1.x, v1.y);
                     if (k == K) {
                         if (row_in && y >= Y0 && y < Y1) {
-                            float2* uo = reinterpret_cast<float2*>(D.uout) + (long long)y * D.uout_pitch;
-                            if (in0 && xp >= K * RAD && xp < K * RAD + BW)
-                                uo[ox + xp] = add2(v0, ref);
+                            float2* uo = reinterpret_cast<float2*>(D.uout);
+                            const long long uoo = (long long)y * D.uout_pitch + ox + xp;
+                            const long long NUO = (long long)h * D.uout_pitch;
+                            (void)NUO;
+                            if (in0 && xp >= K * RAD && xp < K * RAD + BW) PANO_AT(uo, uoo, NUO, 153) = add2(v0, ref);
                             if (in1 && xp + 1 >= K * RAD && xp + 1 < K * RAD + BW)
-                                uo[ox + xp + 1] = add2(v1, ref);
+                                PANO_AT(uo, uoo + 1, NUO, 154) = add2(v1, ref);
                         }
                     } else {
                         // products of stage k+1 at the same two pixels
-                        const float4 g4 = *reinterpret_cast<const float4*>(sG + srow + xp);
-                        const float2 t2 = *reinterpret_cast<const float2*>(sT + srow + xp);
+                        const float4 g4 = PANO_VEC(const float4, sG, srow + xp, 2, NR, 155);
+                        const float2 t2 = PANO_VEC(const float2, sT, srow + xp, 2, NR, 156);
                         float2 P0 = make_float2(0.f, 0.f), P1 = make_float2(0.f, 0.f);
                         if (in0) P0 = residual_product<JW, Ts>(box, ox + xp, y, xp, ref, v0, make_float2(g4.x, g4.y), t2.x);
                         if (in1) P1 = residual_product<JW, Ts>(box, ox + xp + 1, y, xp + 1, ref, v1, make_float2(g4.z, g4.w), t2.y);
-                        *reinterpret_cast<float4*>(sP + (2 * RAD + ty) * RW + xp) = make_float4(P0.x, P0.y, P1.x, P1.y);
+                        PANO_VEC(float4, sP, (2 * RAD + ty) * RW + xp, 2, NP, 157) = make_float4(P0.x, P0.y, P1.x, P1.y);
                     }
                 }
             }
@@ -501,11 +522,11 @@ __device__ __forceinline__ void lk_stream_item(const LkArgs& a, int dir, int bx,
                 if constexpr (!kAsyncT) {
                     // the target loads issued before X_K land in the ring now
                     const int yj = a0 + CH + box.fref_y + kMY + 1 + ty;
-                    float* jdst = sJ + ring_slot(yj) * JW;
+                    const int jdo = ring_slot(yj) * JW;
 #pragma unroll
                     for (int q = 0; q < kJPT; ++q) {
                         const int bc = tx + q * TX;
-                        if (bc < JW) jdst[bc] = jnext[q];
+                        if (bc < JW) PANO_AT(sJ, jdo + bc, NJ, 158) = jnext[q];
                     }
                 }
             }

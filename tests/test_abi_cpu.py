@@ -138,6 +138,14 @@ def test_compose_pair_rejects_bad_arguments_before_any_launch():
                                  0x60000, 0, 0, 8, 8, ctypes.byref(out), None) == inv
 
 
+def test_release_build_has_no_index_checks():
+    lib = binding.load_library()
+    out = (ctypes.c_uint * 4)(7, 7, 7, 7)
+    assert lib.pano_debug_bounds(out) == binding.PANO_ERR_UNSUPPORTED
+    assert tuple(out) == (0, 0, 0, 0)
+    assert lib.pano_debug_bounds(None) == binding.PANO_ERR_INVALID_ARG
+
+
 def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(binding, "_lib", None)
     with pytest.raises(binding.PanoError):
