@@ -45,10 +45,10 @@ SMALL_TILE_PIXELS = 16000    # tiled levels below this many pixels use 16 x 8 ti
 # its launches in one step, from an ncu capture of the current kernel with
 # float32 pyramid planes (the 16-bit instantiations are other kernels: no
 # figure); None when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (1.188352e6 + 4.644352e6 + 18.469632e6 + 171.617024e6) / 4}
+TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (1.188352e6 + 4.644352e6 + 18.470656e6 + 173.016832e6) / 4}
 # Warp instructions per launch of the dominant kernel from the same capture
 # (smsp__inst_executed.sum, averaged over its launches in one step).
-INST_PER_LAUNCH = {"lk_stream_kernel": (10547162 + 32482633 + 90413525 + 366752745) / 4}
+INST_PER_LAUNCH = {"lk_stream_kernel": (10558682 + 32560009 + 90773349 + 368200597) / 4}
 # One warp instruction per scheduler per cycle, four schedulers per SM.
 SCHEDULERS_PER_SM = 4
 SMS = 152
