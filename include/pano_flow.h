@@ -376,9 +376,12 @@ PANO_API pano_status pano_stage_warp(const pano_image* src, const float* flow, f
 /* ----------------------------------------------------------------------
  * Index checks (debug build only). The `check` variant of the library
  * (build.build(variant="check"), compiled with -DPANO_BOUNDS_CHECK) checks
- * every shared-memory index and every global index of the two LK kernels
- * before the access. An index outside its array is counted, the first one
- * recorded, and the access clamped into the array, so nothing traps.
+ * before the access every shared-memory and global index of the two LK
+ * kernels and of the pyramid kernels, the image gathers of the blends,
+ * the compose and the warp, every index of the distance transform of
+ * Eq. (1) and of the energy and adjoint kernels. An index outside its
+ * array is counted, the first one recorded, and the access clamped into
+ * the array, so nothing traps.
  * pano_debug_bounds copies the record into out[4] = {count, site, index,
  * bound} and clears it; call it after the work has completed (synchronise
  * first). In the normal build it writes zeros and returns UNSUPPORTED.

@@ -644,7 +644,9 @@ pano_status pano_debug_bounds(unsigned* out) {
 #ifdef PANO_BOUNDS_CHECK
     cudaError_t e;
     if ((e = bounds_read_lk_stream(out)) != cudaSuccess || (e = bounds_read_lk_stream_bf16(out)) != cudaSuccess ||
-        (e = bounds_read_lk_stream_f16(out)) != cudaSuccess || (e = bounds_read_lk_tile(out)) != cudaSuccess)
+        (e = bounds_read_lk_stream_f16(out)) != cudaSuccess || (e = bounds_read_lk_tile(out)) != cudaSuccess ||
+        (e = bounds_read_pyramid(out)) != cudaSuccess || (e = bounds_read_blend(out)) != cudaSuccess ||
+        (e = bounds_read_edt(out)) != cudaSuccess || (e = bounds_read_refine(out)) != cudaSuccess)
         return cuda_fail(e, "reading the index-check records");
     return PANO_OK;
 #else

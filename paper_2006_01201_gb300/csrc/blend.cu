@@ -11,6 +11,7 @@
 // FlowMagRL / FlowMagLR are |FlowRtoL(p)| / w and |FlowLtoR(p)| / w. With no
 // Blend array the strip value of Eq. (1) is used, (x + 1) / (w + 1). The
 // softmax is evaluated as the equal logistic form 1 / (1 + e^{sR - sL}).
+#include "bounds.cuh"
 #include "common.cuh"
 
 namespace pano {
@@ -36,9 +37,10 @@ __device__ __forceinline__ uint8_t to_u8_rn(float f) {
 // Bilinear sample of channel k of an interleaved image, raw sample scale
 // (0..255 for u8, as stored for f32).
 template <typename Tv>
-__device__ __forceinline__ float sample_channel(const Tv* __restrict__ base, const Taps& t, int k) {
-    return bilinear_mix(t, sample_f(base[t.o00 + k]), sample_f(base[t.o10 + k]), sample_f(base[t.o01 + k]),
-                        sample_f(base[t.o11 + k]));
+__device__ __forceinline__ float sample_channel(const Tv* __restrict__ base, const Taps& t, int k, long long n) {
+    (void)n;  // elements of the image ((h - 1) rows of its pitch and w C): the bound of the index checks
+    return bilinear_mix(t, sample_f(PANO_AT(base, t.o00 + k, n, 401)), sample_f(PANO_AT(base, t.o10 + k, n, 402)),
+                        sample_f(PANO_AT(base, t.o01 + k, n, 403)), sample_f(PANO_AT(base, t.o11 + k, n, 404)));
 }
 
 // Code 1, Area3 branch, at pixel (x, y) of images L, R (h x w, row pitches
@@ -61,8 +63,8 @@ __device__ __forceinline__ void code1_area3(const Tv* __restrict__ Lb, int pitch
     const float wR = e * wL;
 #pragma unroll
     for (int k = 0; k < C; ++k) {
-        const float cl = sample_channel(Lb, tl, k);
-        const float cr = sample_channel(Rb, tr, k);
+        const float cl = sample_channel(Lb, tl, k, (long long)(h - 1) * pitchL + (long long)w * C);
+        const float cr = sample_channel(Rb, tr, k, (long long)(h - 1) * pitchR + (long long)w * C);
         const float f = fmaf(cl, wL, cr * wR);
         if constexpr (sizeof(Tv) == 1) {
             out[k] = to_u8_rn(f);
@@ -130,16 +132,20 @@ __global__ void __launch_bounds__(256, 8) compose_kernel(ComposeArgs a) {
     Tv* out = reinterpret_cast<Tv*>(static_cast<char*>(a.F) + (long long)y * a.F_pitch_bytes) + (long long)x * C;
     const unsigned char area = a.label[(long long)y * a.label_pitch + x];
     if (area == 1 || area == 2) {
-        const Tv* src = (area == 1 ? Lb + (long long)y * pitchL : Rb + (long long)y * pitchR) + (long long)x * C;
+        const Tv* src = area == 1 ? Lb : Rb;
+        const long long o = (long long)y * (area == 1 ? pitchL : pitchR) + (long long)x * C;
+        const long long n = (long long)(h - 1) * (area == 1 ? pitchL : pitchR) + (long long)w * C;
+        (void)n;
 #pragma unroll
-        for (int k = 0; k < C; ++k) out[k] = src[k];
+        for (int k = 0; k < C; ++k) out[k] = PANO_AT(src, o + k, n, 405);
     } else if (area == 3) {
         float2 rl = make_float2(0.f, 0.f), lr = make_float2(0.f, 0.f);
         const int qy = y - a.fy0, qx = x - a.fx0;
         if ((unsigned)qy < (unsigned)a.fh && (unsigned)qx < (unsigned)a.fw) {
-            const long long q = (long long)qy * a.fw + qx;
-            rl = a.flowRL[q];
-            lr = a.flowLR[q];
+            const long long q = (long long)qy * a.fw + qx, nq = (long long)a.fh * a.fw;
+            (void)nq;
+            rl = PANO_AT(a.flowRL, q, nq, 406);
+            lr = PANO_AT(a.flowLR, q, nq, 407);
         }
         code1_area3<Tv, C>(Lb, pitchL, Rb, pitchR, w, h, x, y, a.blend[(long long)y * a.blend_pitch + x], rl, lr,
                            a.inv_fw, a.k_sharp, a.k_mag, out);
@@ -161,7 +167,7 @@ __global__ void __launch_bounds__(256) warp_kernel(WarpArgs a) {
     const Tv* __restrict__ base = static_cast<const Tv*>(a.src.data);
     float* out = reinterpret_cast<float*>(reinterpret_cast<char*>(a.dst) + (long long)y * a.dst_pitch_bytes) + x * C;
     const float scale = sizeof(Tv) == 1 ? 1.0f / 255.0f : 1.0f;  // samples widened by sample_f
-    for (int k = 0; k < C; ++k) out[k] = sample_channel(base, t, k) * scale;
+    for (int k = 0; k < C; ++k) out[k] = sample_channel(base, t, k, (long long)(h - 1) * pitch + (long long)w * C) * scale;
 }
 
 }  // namespace
@@ -202,6 +208,8 @@ cudaError_t launch_rig_blend(const RigBlendArgs& args, cudaStream_t s) {
     }
     return cudaGetLastError();
 }
+
+PANO_BOUNDS_READER(bounds_read_blend)
 
 cudaError_t launch_compose(const ComposeArgs& a, cudaStream_t s) {
     dim3 block(32, 8);

@@ -30,6 +30,18 @@ __device__ __forceinline__ T* checked_at(T* base, long long off, long long n, in
     }
     return base + off;
 }
+// an index i into [0, n): an image column or row before its address is formed
+__device__ __forceinline__ int checked_idx(int i, int n, int site) {
+    if (i < 0 || i >= n) {
+        if (atomicAdd(&g_pano_oob[0], 1u) == 0u) {
+            g_pano_oob[1] = (unsigned)site;
+            g_pano_oob[2] = (unsigned)i;
+            g_pano_oob[3] = (unsigned)n;
+        }
+        i = i < 0 ? 0 : n - 1;
+    }
+    return i;
+}
 // `width` consecutive elements from `off` (a vector access): a clamped
 // offset is rounded down to a multiple of `width`, so it keeps the
 // alignment that every valid offset of such an access has.
@@ -47,6 +59,8 @@ __device__ __forceinline__ T* checked_vec(T* base, long long off, int width, lon
 }
 }  // namespace pano
 #define PANO_AT(base, off, n, site) (*pano::checked_at((base), (long long)(off), (long long)(n), (site)))
+// an index i into [0, n) (an image column or row before its address is formed)
+#define PANO_IDX(i, n, site) pano::checked_idx((i), (n), (site))
 // a vector of `width` elements of base's type starting at `off`
 #define PANO_VEC(VT, base, off, width, n, site) \
     (*reinterpret_cast<VT*>(pano::checked_vec((base), (long long)(off), (width), (long long)(n), (site))))
@@ -63,6 +77,7 @@ __device__ __forceinline__ T* checked_vec(T* base, long long off, int width, lon
     }
 #else
 #define PANO_AT(base, off, n, site) ((base)[off])
+#define PANO_IDX(i, n, site) (i)
 #define PANO_VEC(VT, base, off, width, n, site) (*reinterpret_cast<VT*>((base) + (off)))
 #define PANO_BOUNDS_READER(fn) \
     cudaError_t fn(unsigned*) { return cudaSuccess; }

@@ -296,6 +296,10 @@ cudaError_t bounds_read_lk_stream(unsigned* out);
 cudaError_t bounds_read_lk_stream_bf16(unsigned* out);
 cudaError_t bounds_read_lk_stream_f16(unsigned* out);
 cudaError_t bounds_read_lk_tile(unsigned* out);
+cudaError_t bounds_read_pyramid(unsigned* out);
+cudaError_t bounds_read_blend(unsigned* out);
+cudaError_t bounds_read_edt(unsigned* out);
+cudaError_t bounds_read_refine(unsigned* out);
 
 // Stores the message that pano_last_error() returns on the calling thread.
 void set_last_error(const char* msg);

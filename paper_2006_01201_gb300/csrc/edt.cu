@@ -25,6 +25,7 @@
 
 #include <climits>
 
+#include "bounds.cuh"
 #include "common.cuh"
 #include "ctx.h"
 #include "pano_flow.h"
@@ -43,34 +44,39 @@ __global__ void __launch_bounds__(kColThreads) edt_cols_kernel(const unsigned ch
                                                                int* __restrict__ gR) {
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     if (x >= w) return;
+    const long long nl = (long long)(h - 1) * pitch + w, ng = (long long)h * w;  // label and g elements
+    (void)nl;
+    (void)ng;
     int dl = kNone, dr = kNone;
     for (int y = 0; y < h; ++y) {
-        const unsigned char a = __ldg(label + (long long)y * pitch + x);
+        const unsigned char a = __ldg(&PANO_AT(label, (long long)y * pitch + x, nl, 501));
         dl = a == 1 ? 0 : min(dl + 1, kNone);
         dr = a == 2 ? 0 : min(dr + 1, kNone);
-        gL[(long long)y * w + x] = dl;
-        gR[(long long)y * w + x] = dr;
+        PANO_AT(gL, (long long)y * w + x, ng, 502) = dl;
+        PANO_AT(gR, (long long)y * w + x, ng, 502) = dr;
     }
     dl = dr = kNone;
     for (int y = h - 1; y >= 0; --y) {
-        const unsigned char a = __ldg(label + (long long)y * pitch + x);
+        const unsigned char a = __ldg(&PANO_AT(label, (long long)y * pitch + x, nl, 503));
         dl = a == 1 ? 0 : min(dl + 1, kNone);
         dr = a == 2 ? 0 : min(dr + 1, kNone);
         const long long o = (long long)y * w + x;
-        gL[o] = min(gL[o], dl);
-        gR[o] = min(gR[o], dr);
+        PANO_AT(gL, o, ng, 504) = min(PANO_AT(gL, o, ng, 504), dl);
+        PANO_AT(gR, o, ng, 504) = min(PANO_AT(gR, o, ng, 504), dr);
     }
 }
 
-// Parabola of site q: f(q) + (x - q)^2 with f = g^2.
-__device__ __forceinline__ long long site_f(const int* __restrict__ g, int q) {
-    const long long v = g[q];
+// Parabola of site q of a row of w columns: f(q) + (x - q)^2 with f = g^2.
+__device__ __forceinline__ long long site_f(const int* __restrict__ g, int w, int q) {
+    (void)w;
+    const long long v = PANO_AT(g, q, w, 505);
     return v * v;
 }
 
 // Intersection abscissa of the parabolas of sites p < q as num / den (den > 0).
-__device__ __forceinline__ void intersect(const int* __restrict__ g, int p, int q, long long* num, long long* den) {
-    *num = (site_f(g, q) + (long long)q * q) - (site_f(g, p) + (long long)p * p);
+__device__ __forceinline__ void intersect(const int* __restrict__ g, int w, int p, int q, long long* num,
+                                          long long* den) {
+    *num = (site_f(g, w, q) + (long long)q * q) - (site_f(g, w, p) + (long long)p * p);
     *den = 2LL * (q - p);
 }
 
@@ -79,38 +85,40 @@ __device__ __forceinline__ void intersect(const int* __restrict__ g, int p, int 
 __device__ int build_envelope(const int* __restrict__ g, int w, int* __restrict__ v) {
     int k = -1;
     for (int q = 0; q < w; ++q) {
-        if (g[q] >= kNone) continue;
+        if (PANO_AT(g, q, w, 506) >= kNone) continue;
         if (k < 0) {
-            v[++k] = q;
+            PANO_AT(v, ++k, w, 507) = q;
             continue;
         }
         // drop envelope parabolas that the new one hides: while the new
         // intersection lies at or left of the start of the last parabola
         while (k >= 1) {
             long long n1, d1, n0, d0;
-            intersect(g, v[k], q, &n1, &d1);      // s(v[k], q)
-            intersect(g, v[k - 1], v[k], &n0, &d0);  // z[k] = s(v[k-1], v[k])
+            intersect(g, w, PANO_AT(v, k, w, 508), q, &n1, &d1);  // s(v[k], q)
+            intersect(g, w, PANO_AT(v, k - 1, w, 508), PANO_AT(v, k, w, 508), &n0, &d0);  // z[k] = s(v[k-1], v[k])
             if (n1 * d0 <= n0 * d1) --k;
             else break;
         }
-        v[++k] = q;
+        PANO_AT(v, ++k, w, 507) = q;
     }
     return k;
 }
 
 // Squared distance at column x from an envelope of k + 1 sites.
-__device__ __forceinline__ long long envelope_at(const int* __restrict__ g, const int* __restrict__ v, int k, int x) {
+__device__ __forceinline__ long long envelope_at(const int* __restrict__ g, const int* __restrict__ v, int w, int k,
+                                                int x) {
     // largest j with z[j] <= x, z[0] = -infinity, z[j] = s(v[j-1], v[j])
     int lo = 0, hi = k;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         long long n, d;
-        intersect(g, v[mid - 1], v[mid], &n, &d);
+        intersect(g, w, PANO_AT(v, mid - 1, w, 509), PANO_AT(v, mid, w, 509), &n, &d);
         if (n <= (long long)x * d) lo = mid;
         else hi = mid - 1;
     }
-    const long long dx = x - v[lo];
-    return dx * dx + site_f(g, v[lo]);
+    const int q = PANO_AT(v, lo, w, 509);
+    const long long dx = x - q;
+    return dx * dx + site_f(g, w, q);
 }
 
 // Row pass and Eq. (1): one CTA per row. Warp 0 builds the Area1 envelope,
@@ -137,7 +145,7 @@ __global__ void __launch_bounds__(kRowThreads) edt_rows_blend_kernel(const unsig
     const unsigned char* lab = label + (long long)y * pitch;
     float* out = blend + (long long)y * blend_pitch;
     for (int x = threadIdx.x; x < w; x += blockDim.x) {
-        const unsigned char a = lab[x];
+        const unsigned char a = PANO_AT(lab, x, w, 510);
         float b;
         if (a == 1) {
             b = 0.f;
@@ -148,18 +156,20 @@ __global__ void __launch_bounds__(kRowThreads) edt_rows_blend_kernel(const unsig
             else if (kL < 0) b = 1.f;
             else if (kR < 0) b = 0.f;
             else {
-                const float dl = sqrtf((float)envelope_at(rowL, vL, kL, x));
-                const float dr = sqrtf((float)envelope_at(rowR, vR, kR, x));
+                const float dl = sqrtf((float)envelope_at(rowL, vL, w, kL, x));
+                const float dr = sqrtf((float)envelope_at(rowR, vR, w, kR, x));
                 b = dl / (dl + dr);
             }
         } else {
             b = 0.5f;
         }
-        out[x] = b;
+        PANO_AT(out, x, w, 511) = b;
     }
 }
 
 }  // namespace
+
+PANO_BOUNDS_READER(bounds_read_edt)
 
 size_t blend_coeff_scratch_bytes(int h, int w) { return (size_t)2 * h * w * sizeof(int); }
 

@@ -6,6 +6,7 @@
 // columns (level size ceil(h/2) x ceil(w/2)). Level 0 is the BT.601 luma of
 // the unit-scaled strip. Levels are stored as float32, bfloat16 or binary16
 // (rounded to nearest even); every sum is formed in FP32.
+#include "bounds.cuh"
 #include "common.cuh"
 
 namespace pano {
@@ -29,6 +30,7 @@ __device__ __forceinline__ float byte_f(uint32_t b) { return __uint_as_float(0x4
 __device__ __forceinline__ float luma3(float r, float g, float b) { return fmaf(0.114f, b, fmaf(0.587f, g, 0.299f * r)); }
 
 __device__ __forceinline__ float luma_at(const ImageDesc& in, const unsigned char* row, int x) {
+    x = PANO_IDX(x, in.w, 315);
     if (in.dtype == 0) {
         if (in.c == 3) {
             const uint8_t* px = row + 3 * x;
@@ -44,6 +46,7 @@ __device__ __forceinline__ float luma_at(const ImageDesc& in, const unsigned cha
 // Luma of the four pixels x .. x+3 of a row (all inside the row): 12 aligned
 // bytes for u8 RGB when the address allows it, else one pixel at a time.
 __device__ __forceinline__ void luma4(const ImageDesc& in, const unsigned char* row, int x, float (&v)[4]) {
+    x = PANO_IDX(x, in.w - 3, 316);  // pixels x .. x+3
     if (in.dtype == 0 && in.c == 3 && ((((uintptr_t)row) + 3 * x) & 3) == 0) {
         const uint32_t* p = reinterpret_cast<const uint32_t*>(row + 3 * x);
         const uint32_t w0 = __ldg(p), w1 = __ldg(p + 1), w2 = __ldg(p + 2);
@@ -151,7 +154,12 @@ __device__ __forceinline__ void reduce_staged(const float (*s_src)[kPdSW], float
     for (int i = tid; i < kPdTH * kPdSW; i += 256) {
         int r = i / kPdSW, c = i - r * kPdSW;
         int sr = 2 * r + 2;
-        s_v[r][c] = reduce5(s_src[sr - 2][c], s_src[sr - 1][c], s_src[sr][c], s_src[sr + 1][c], s_src[sr + 2][c]);
+        const float* S = &s_src[0][0];
+        constexpr int NS = kPdSH * kPdSW;
+        PANO_AT(&s_v[0][0], r * (kPdSW + 1) + c, kPdTH * (kPdSW + 1), 311) =
+            reduce5(PANO_AT(S, (sr - 2) * kPdSW + c, NS, 312), PANO_AT(S, (sr - 1) * kPdSW + c, NS, 312),
+                    PANO_AT(S, sr * kPdSW + c, NS, 312), PANO_AT(S, (sr + 1) * kPdSW + c, NS, 312),
+                    PANO_AT(S, (sr + 2) * kPdSW + c, NS, 312));
     }
     __syncthreads();
     const int x = tid & (kPdTW - 1);
@@ -162,8 +170,11 @@ __device__ __forceinline__ void reduce_staged(const float (*s_src)[kPdSW], float
         for (int r = tid / kPdTW; r < kPdTH; r += 256 / kPdTW) {
             const int yd = yd0 + r;
             if (yd >= hd) break;
-            const float* v = s_v[r];
-            dst[(long long)yd * dst_pitch + xd] = from_f32<Ts>(reduce5(v[c - 2], v[c - 1], v[c], v[c + 1], v[c + 2]));
+            const float* V = &s_v[0][0];
+            const int o = r * (kPdSW + 1) + c, NV = kPdTH * (kPdSW + 1);
+            PANO_AT(dst, (long long)yd * dst_pitch + xd, (long long)hd * dst_pitch, 313) = from_f32<Ts>(
+                reduce5(PANO_AT(V, o - 2, NV, 314), PANO_AT(V, o - 1, NV, 314), PANO_AT(V, o, NV, 314),
+                        PANO_AT(V, o + 1, NV, 314), PANO_AT(V, o + 2, NV, 314)));
         }
     }
 }
@@ -186,18 +197,20 @@ __global__ void __launch_bounds__(256) pyr_down_kernel(const __grid_constant__ P
     const bool vec = ((((uintptr_t)src) & (4 * sizeof(Ts) - 1)) == 0) && (src_pitch & 3) == 0;
     for (int i = tid; i < kPdSH * kPdQ; i += 256) {
         const int r = i / kPdQ, q = i - r * kPdQ;
-        const int sy = min(max(sy0 + r, 0), h - 1);
+        const int sy = PANO_IDX(min(max(sy0 + r, 0), h - 1), h, 317);
         const int sx = cx0 + 4 * q;
-        const Ts* row = src + (long long)sy * src_pitch;
-        float* o = &s_src[r][4 * q];
+        const long long ro = (long long)sy * src_pitch;
+        const long long ns = (long long)(h - 1) * src_pitch + w;  // elements of the plane
+        (void)ns;
+        float* o = &PANO_VEC(float, &s_src[0][0], r * kPdSW + 4 * q, 4, kPdSH * kPdSW, 318);
         if (vec && sx >= 0 && sx + 3 < w) {
             using V = typename Vec4Of<Ts>::type;
-            const V v = __ldg(reinterpret_cast<const V*>(row + sx));
+            const V v = __ldg(&PANO_VEC(const V, src, ro + sx, 4, ns, 319));
             if constexpr (sizeof(Ts) == 4) widen4(v, o);
             else widen4<Ts>(v, o);
         } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) o[k] = ld_f32(row + min(max(sx + k, 0), w - 1));
+            for (int k = 0; k < 4; ++k) o[k] = ld_f32(&PANO_AT(src, ro + min(max(sx + k, 0), w - 1), ns, 320));
         }
     }
     __syncthreads();
@@ -228,7 +241,7 @@ __global__ void __launch_bounds__(256) luma_reduce_kernel(const __grid_constant_
     for (int i = tid; i < kPdSH * kPdQ; i += 256) {
         const int r = i / kPdQ, q = i - r * kPdQ;
         const int yy = sy0 + r;
-        const int sy = min(max(yy, 0), h - 1);
+        const int sy = PANO_IDX(min(max(yy, 0), h - 1), h, 321);
         const int sx = cx0 + 4 * q;
         const unsigned char* row = static_cast<const unsigned char*>(in.data) + (long long)sy * in.pitch_bytes;
         float v[4];
@@ -240,16 +253,18 @@ __global__ void __launch_bounds__(256) luma_reduce_kernel(const __grid_constant_
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = to_f32(from_f32<Ts>(v[k]));  // the stored level-0 value
-        float* o = &s_src[r][4 * q];
+        float* o = &PANO_VEC(float, &s_src[0][0], r * kPdSW + 4 * q, 4, kPdSH * kPdSW, 322);
 #pragma unroll
         for (int k = 0; k < 4; ++k) o[k] = v[k];
         // level-0 pixels owned by this block
         if (r >= 2 && r < 2 + 2 * kPdTH && yy < h && q >= 1 && q <= kPdTW / 2 && sx < w) {
-            Ts* orow = l0 + (long long)yy * p0;
+            const long long ro = (long long)yy * p0;
+            const long long n0 = (long long)(h - 1) * p0 + w;  // elements of level 0
+            (void)n0;
             if (sx + 3 < w) {
-                store4(orow + sx, v);
+                store4(&PANO_VEC(Ts, l0, ro + sx, 1, n0 - 3, 323), v);   // elements sx .. sx+3
             } else {
-                for (int k = 0; k < 4 && sx + k < w; ++k) orow[sx + k] = from_f32<Ts>(v[k]);
+                for (int k = 0; k < 4 && sx + k < w; ++k) PANO_AT(l0, ro + sx + k, n0, 324) = from_f32<Ts>(v[k]);
             }
         }
     }
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(256) pyr_tail_kernel(const __grid_constant__ P
         for (int i = tid; i < n * n; i += 256) {
             const int r = i / n, c = i - r * n;
             const int y = min(max(Oy(M) + r, 0), H(M) - 1), x = min(max(Ox(M) + c, 0), W(M) - 1);
-            b[i] = ld_f32(src + (long long)y * pitch + x);
+            PANO_AT(b, i, n * n, 301) = ld_f32(&PANO_AT(src, (long long)y * pitch + x, (long long)H(M) * pitch, 302));
         }
     }
     __syncthreads();
@@ -326,8 +341,10 @@ __global__ void __launch_bounds__(256) pyr_tail_kernel(const __grid_constant__ P
         // along y at the even rows of the finer level
         for (int i = tid; i < nc * nf; i += 256) {
             const int r = i / nf, q = i - r * nf;
-            const float* col = f + 2 * r * nf + q;
-            tmp[i] = reduce5(col[0], col[nf], col[2 * nf], col[3 * nf], col[4 * nf]);
+            const int o = 2 * r * nf + q, nn = nf * nf;
+            PANO_AT(tmp, i, tail_tmp(M), 303) =
+                reduce5(PANO_AT(f, o, nn, 304), PANO_AT(f, o + nf, nn, 304), PANO_AT(f, o + 2 * nf, nn, 304),
+                        PANO_AT(f, o + 3 * nf, nn, 304), PANO_AT(f, o + 4 * nf, nn, 304));
         }
         __syncthreads();
         // along x at the even columns, for the pixels inside the level
@@ -335,8 +352,10 @@ __global__ void __launch_bounds__(256) pyr_tail_kernel(const __grid_constant__ P
             const int r = i / nc, q = i - r * nc;
             const int y = Oy(d) + r, x = Ox(d) + q;
             if (y < 0 || y >= H(d) || x < 0 || x >= W(d)) continue;
-            const float* v = tmp + r * nf + 2 * q;
-            c[i] = to_f32(from_f32<Ts>(reduce5(v[0], v[1], v[2], v[3], v[4])));
+            const int o = r * nf + 2 * q, nt = tail_tmp(M);
+            PANO_AT(c, i, nc * nc, 305) = to_f32(from_f32<Ts>(
+                reduce5(PANO_AT(tmp, o, nt, 306), PANO_AT(tmp, o + 1, nt, 306), PANO_AT(tmp, o + 2, nt, 306),
+                        PANO_AT(tmp, o + 3, nt, 306), PANO_AT(tmp, o + 4, nt, 306))));
         }
         __syncthreads();
         // the replicate border: pixels outside the level take the clamped pixel
@@ -345,7 +364,7 @@ __global__ void __launch_bounds__(256) pyr_tail_kernel(const __grid_constant__ P
             const int y = Oy(d) + r, x = Ox(d) + q;
             if (y >= 0 && y < H(d) && x >= 0 && x < W(d)) continue;
             const int cy = min(max(y, 0), H(d) - 1), cx = min(max(x, 0), W(d) - 1);
-            c[i] = c[(cy - Oy(d)) * nc + (cx - Ox(d))];
+            PANO_AT(c, i, nc * nc, 307) = PANO_AT(c, (cy - Oy(d)) * nc + (cx - Ox(d)), nc * nc, 308);
         }
         // the owned pixels of this level
         Ts* __restrict__ dst = static_cast<Ts*>(a.dst[z][M - 1 - d]);
@@ -356,7 +375,8 @@ __global__ void __launch_bounds__(256) pyr_tail_kernel(const __grid_constant__ P
             const int r = i / t, q = i - r * t;
             const int y = y0 + r, x = x0 + q;
             if (y >= H(d) || x >= W(d)) continue;
-            dst[(long long)y * dp + x] = from_f32<Ts>(c[(y - Oy(d)) * nc + (x - Ox(d))]);
+            PANO_AT(dst, (long long)y * dp + x, (long long)H(d) * dp, 309) =
+                from_f32<Ts>(PANO_AT(c, (y - Oy(d)) * nc + (x - Ox(d)), nc * nc, 310));
         }
         __syncthreads();
     }
@@ -439,6 +459,8 @@ cudaError_t launch_luma_reduce(const LumaReduceArgs& a, cudaStream_t s) {
     }
     return cudaGetLastError();
 }
+
+PANO_BOUNDS_READER(bounds_read_pyramid)
 
 cudaError_t launch_luma(const LumaArgs& a, cudaStream_t s) {
     if (a.count < 1 || a.count > kMaxPlanes) return cudaErrorInvalidValue;

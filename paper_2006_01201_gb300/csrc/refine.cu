@@ -10,6 +10,7 @@
 // the GPU, used by finite-difference checks), dE/du, dE/dT and dE/dJ, and the
 // transpose of the pyramid REDUCE so that gradients can be carried to
 // full-resolution images without storing the pyramid.
+#include "bounds.cuh"
 #include "common.cuh"
 
 namespace pano {
@@ -32,7 +33,12 @@ __global__ void __launch_bounds__(kEgThreads) energy_grad_kernel(EnergyArgs a) {
     double e = 0.0;
     if (x < w && y < h) {
         const long long p = (long long)y * w + x;
-        const float2 u = reinterpret_cast<const float2*>(a.u)[p];
+        const long long nf = (long long)h * w;                      // flow / gradient elements
+        const long long nj = (long long)(h - 1) * a.pitch + w;      // elements of T and J
+        (void)nf;
+        (void)nj;
+        const float2* U = reinterpret_cast<const float2*>(a.u);
+        const float2 u = PANO_AT(U, p, nf, 601);
         // bilinear sample of J at p + u and its derivative along x and y
         const float ox = fminf(fmaxf(u.x, -(float)(w + 2)), (float)(w + 2));
         const float oy = fminf(fmaxf(u.y, -(float)(h + 2)), (float)(h + 2));
@@ -41,38 +47,37 @@ __global__ void __launch_bounds__(kEgThreads) energy_grad_kernel(EnergyArgs a) {
         const int x0 = x + (int)fxf, y0 = y + (int)fyf;
         const int xa = min(max(x0, 0), w - 1), xb = min(max(x0 + 1, 0), w - 1);
         const int ya = min(max(y0, 0), h - 1), yb = min(max(y0 + 1, 0), h - 1);
-        const float* Ja = a.J + (long long)ya * a.pitch;
-        const float* Jb = a.J + (long long)yb * a.pitch;
-        const float i00 = __ldg(Ja + xa), i10 = __ldg(Ja + xb), i01 = __ldg(Jb + xa), i11 = __ldg(Jb + xb);
+        const long long ra = (long long)ya * a.pitch, rb = (long long)yb * a.pitch;
+        const float i00 = __ldg(&PANO_AT(a.J, ra + xa, nj, 602)), i10 = __ldg(&PANO_AT(a.J, ra + xb, nj, 602));
+        const float i01 = __ldg(&PANO_AT(a.J, rb + xa, nj, 602)), i11 = __ldg(&PANO_AT(a.J, rb + xb, nj, 602));
         const float top = fmaf(fx, i10 - i00, i00), bot = fmaf(fx, i11 - i01, i01);
         const float Jw = fmaf(fy, bot - top, top);
-        const float r = Jw - __ldg(a.T + (long long)y * a.pitch + x);
+        const float r = Jw - __ldg(&PANO_AT(a.T, (long long)y * a.pitch + x, nj, 603));
         e = (double)r * (double)r;
         // smoothness: forward differences to the right and downwards
-        const float2* U = reinterpret_cast<const float2*>(a.u);
         float2 lap = make_float2(0.f, 0.f);
         double es = 0.0;
         if (x < w - 1) {
-            const float2 n = U[p + 1];
+            const float2 n = PANO_AT(U, p + 1, nf, 604);
             const float dx0 = n.x - u.x, dx1 = n.y - u.y;
             es += (double)dx0 * dx0 + (double)dx1 * dx1;
             lap.x -= dx0;
             lap.y -= dx1;
         }
         if (y < h - 1) {
-            const float2 n = U[p + w];
+            const float2 n = PANO_AT(U, p + w, nf, 605);
             const float dy0 = n.x - u.x, dy1 = n.y - u.y;
             es += (double)dy0 * dy0 + (double)dy1 * dy1;
             lap.x -= dy0;
             lap.y -= dy1;
         }
         if (x > 0) {
-            const float2 n = U[p - 1];
+            const float2 n = PANO_AT(U, p - 1, nf, 606);
             lap.x += u.x - n.x;
             lap.y += u.y - n.y;
         }
         if (y > 0) {
-            const float2 n = U[p - w];
+            const float2 n = PANO_AT(U, p - w, nf, 607);
             lap.x += u.x - n.x;
             lap.y += u.y - n.y;
         }
@@ -80,17 +85,17 @@ __global__ void __launch_bounds__(kEgThreads) energy_grad_kernel(EnergyArgs a) {
         if (a.grad_u) {
             const float jdx = fmaf(fy, (i11 - i01) - (i10 - i00), i10 - i00);
             const float jdy = fmaf(fx, (i11 - i10) - (i01 - i00), i01 - i00);
-            reinterpret_cast<float2*>(a.grad_u)[p] =
+            PANO_AT(reinterpret_cast<float2*>(a.grad_u), p, nf, 608) =
                 make_float2(2.f * r * jdx + 2.f * a.alpha * lap.x, 2.f * r * jdy + 2.f * a.alpha * lap.y);
         }
-        if (a.grad_T) a.grad_T[p] = -2.f * r;
+        if (a.grad_T) PANO_AT(a.grad_T, p, nf, 609) = -2.f * r;
         if (a.grad_J) {
             const float g = 2.f * r;
             float* GJ = a.grad_J;
-            atomicAdd(GJ + (long long)ya * w + xa, g * (1.f - fy) * (1.f - fx));
-            atomicAdd(GJ + (long long)ya * w + xb, g * (1.f - fy) * fx);
-            atomicAdd(GJ + (long long)yb * w + xa, g * fy * (1.f - fx));
-            atomicAdd(GJ + (long long)yb * w + xb, g * fy * fx);
+            atomicAdd(&PANO_AT(GJ, (long long)ya * w + xa, nf, 610), g * (1.f - fy) * (1.f - fx));
+            atomicAdd(&PANO_AT(GJ, (long long)ya * w + xb, nf, 610), g * (1.f - fy) * fx);
+            atomicAdd(&PANO_AT(GJ, (long long)yb * w + xa, nf, 610), g * fy * (1.f - fx));
+            atomicAdd(&PANO_AT(GJ, (long long)yb * w + xb, nf, 610), g * fy * fx);
         }
     }
     if (a.energy) {
@@ -137,19 +142,23 @@ __global__ void __launch_bounds__(256) pyr_down_adjoint_kernel(const float* __re
     float wy[4], wx[4];
     reduce_taps(y, h, hd, dy, wy);
     reduce_taps(x, w, wd, dx, wx);
+    const long long nd = (long long)(hd - 1) * dst_pitch + wd;  // elements of the gradient of the output
+    (void)nd;
     float acc = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const float* row = gdst + (long long)dy[i] * dst_pitch;
+        const long long ro = (long long)dy[i] * dst_pitch;
         float racc = 0.f;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) racc = fmaf(wx[j], __ldg(row + dx[j]), racc);
+        for (int j = 0; j < 4; ++j) racc = fmaf(wx[j], __ldg(&PANO_AT(gdst, ro + dx[j], nd, 611)), racc);
         acc = fmaf(wy[i], racc, acc);
     }
-    gsrc[(long long)y * src_pitch + x] = acc;
+    PANO_AT(gsrc, (long long)y * src_pitch + x, (long long)(h - 1) * src_pitch + w, 612) = acc;
 }
 
 }  // namespace
+
+PANO_BOUNDS_READER(bounds_read_refine)
 
 cudaError_t launch_energy_grad(const EnergyArgs& a, cudaStream_t s) {
     cudaError_t e;

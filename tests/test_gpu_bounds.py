@@ -1,11 +1,13 @@
-"""Index checks of the LK kernels on odd shapes.
+"""Index checks of every kernel of the library on odd shapes.
 
 The check variant of the library (build variant "check") checks every
-shared-memory and global index of the streamed and the tiled LK kernels
-before the access; an index outside its array is recorded and clamped
-instead of trapping (pano_debug_bounds). Every run below must leave the
-record empty and give exactly the flows of the release library: the checks
-change no arithmetic.
+shared-memory and global index of the streamed and the tiled LK kernels,
+the pyramid kernels, the distance transform of Eq. (1) and the energy and
+adjoint kernels, and the bilinear gathers of the warp, the strip blend and
+the canvas compose, before the access; an index outside its array is recorded
+and clamped instead of trapping (pano_debug_bounds). Every run below must
+leave the record empty and give exactly the results of the release library:
+the checks change no arithmetic.
 """
 import numpy as np
 import pytest
@@ -120,3 +122,88 @@ def test_rig_keeps_every_index_in_bounds(libs, monkeypatch):
     assert torch.equal(ca, cb)
     for (alr, arl), (blr, brl) in zip(fa, fb):
         assert torch.equal(alr, blr) and torch.equal(arl, brl)
+
+
+@pytest.mark.parametrize("h,w,nlev", [(17, 33, 4), (5, 7, 3), (263, 129, 6), (1, 300, 2), (96, 1, 2)])
+def test_pyramid_keeps_every_index_in_bounds(libs, monkeypatch, h, w, nlev):
+    img = torch.from_numpy(_texture(h, w, 3, 5)).to(DEV)
+
+    def run():
+        Y, Y1 = binding.stage_luma_pyr(img)
+        return [Y, Y1] + binding.stage_pyramid(Y, nlev)
+
+    a, b, rec = _run_both(libs, monkeypatch, run)
+    assert rec[0] == 0, f"{rec[0]} indices out of bounds, first at site {rec[1]}: {rec[2]} of {rec[3]}"
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("h,w,c", [(37, 61, 3), (9, 250, 1), (120, 97, 3)])
+def test_blends_and_warp_keep_every_index_in_bounds(libs, monkeypatch, h, w, c):
+    m = 6
+    canvas_L = torch.from_numpy(_texture(h, w + 2 * m, c, 6)).to(DEV)
+    canvas_R = torch.from_numpy(_texture(h, w + 2 * m, c, 7)).to(DEV)
+    L, R = canvas_L[:, m:m + w], canvas_R[:, m:m + w]            # strided strips
+    g = np.random.default_rng(8)
+    lr = torch.from_numpy(g.normal(0, 25, (h, w, 2)).astype(np.float32)).to(DEV)   # samples far outside
+    rl = torch.from_numpy(g.normal(0, 25, (h, w, 2)).astype(np.float32)).to(DEV)
+    lab = np.full((h, w + 2 * m), 3, np.uint8)
+    lab[:, :m], lab[:, m + w:] = 1, 2
+    lab[0, :3] = 0
+    labd = torch.from_numpy(lab).to(DEV)
+    B = torch.from_numpy(np.tile(np.linspace(0, 1, w + 2 * m, dtype=np.float32), (h, 1))).to(DEV)
+
+    def run():
+        with binding.FlowContext(binding.Params(), max_h=h, max_w=w, max_c=c) as ctx:
+            F = ctx.blend_pair(L, R, lr, rl)
+        G = binding.compose_pair(canvas_L, canvas_R, labd, B, lr, rl, origin=(0, m))
+        Wp = binding.stage_warp(L, lr, 0.7)
+        return F, G, Wp
+
+    a, b, rec = _run_both(libs, monkeypatch, run)
+    assert rec[0] == 0, f"{rec[0]} indices out of bounds, first at site {rec[1]}: {rec[2]} of {rec[3]}"
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
+@pytest.mark.parametrize("h,w,kind", [(37, 61, "blobs"), (1, 200, "blobs"), (150, 1, "blobs"), (40, 90, "no_area1"),
+                                      (33, 47, "area3_only"), (64, 300, "single_sites")])
+def test_distance_transform_keeps_every_index_in_bounds(libs, monkeypatch, h, w, kind):
+    g = np.random.default_rng(9)
+    if kind == "blobs":
+        lab = g.choice(np.array([0, 1, 2, 3, 3, 3], np.uint8), size=(h, w))
+    elif kind == "no_area1":
+        lab = np.where(g.uniform(size=(h, w)) < 0.05, 2, 3).astype(np.uint8)
+    elif kind == "area3_only":
+        lab = np.full((h, w), 3, np.uint8)
+    else:   # one Area1 and one Area2 pixel per row, so every envelope has one site per column band
+        lab = np.full((h, w), 3, np.uint8)
+        lab[np.arange(h), g.integers(0, w, h)] = 1
+        lab[np.arange(h), g.integers(0, w, h)] = 2
+    canvas = torch.zeros((h, w + 5), dtype=torch.uint8, device=DEV)
+    canvas[:, 2:2 + w] = torch.from_numpy(lab).to(DEV)
+    label = canvas[:, 2:2 + w]                                  # a strided label
+
+    a, b, rec = _run_both(libs, monkeypatch, lambda: binding.blend_coeff(label))
+    assert rec[0] == 0, f"{rec[0]} indices out of bounds, first at site {rec[1]}: {rec[2]} of {rec[3]}"
+    assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("h,w", [(29, 45), (1, 70), (64, 1), (130, 257)])
+def test_energy_and_adjoint_keep_every_index_in_bounds(libs, monkeypatch, h, w):
+    T = torch.from_numpy(_texture(h, w, 1, 11)).to(DEV)
+    J = torch.from_numpy(_texture(h, w, 1, 12)).to(DEV)
+    g = np.random.default_rng(13)
+    u = torch.from_numpy(g.normal(0, 40, (h, w, 2)).astype(np.float32)).to(DEV)   # samples far outside
+    gd = torch.from_numpy(g.normal(0, 1, ((h + 1) // 2, (w + 1) // 2)).astype(np.float32)).to(DEV)
+
+    def run():
+        E, gu, gt, gj = binding.energy_grad(T, J, u, 0.3)
+        return E, gu, gt, gj, binding.stage_pyr_down_adjoint(gd, h, w)
+
+    (Ea, gua, gta, gja, ada), (Eb, gub, gtb, gjb, adb), rec = _run_both(libs, monkeypatch, run)
+    assert rec[0] == 0, f"{rec[0]} indices out of bounds, first at site {rec[1]}: {rec[2]} of {rec[3]}"
+    assert torch.equal(gua, gub) and torch.equal(gta, gtb) and torch.equal(ada, adb)
+    # E and dE/dJ are sums by atomics, in no fixed order
+    torch.testing.assert_close(Eb, Ea, rtol=1e-12, atol=0)
+    torch.testing.assert_close(gjb, gja, rtol=1e-5, atol=1e-6)
