@@ -61,6 +61,9 @@ __device__ __forceinline__ T* checked_vec(T* base, long long off, int width, lon
 #define PANO_AT(base, off, n, site) (*pano::checked_at((base), (long long)(off), (long long)(n), (site)))
 // an index i into [0, n) (an image column or row before its address is formed)
 #define PANO_IDX(i, n, site) pano::checked_idx((i), (n), (site))
+// a condition that valid inputs never meet (an iteration limit reached):
+// recorded like an index outside its array, with offset and bound 0
+#define PANO_FLAG(cond, site) ((cond) ? (void)pano::checked_idx(0, 0, (site)) : (void)0)
 // a vector of `width` elements of base's type starting at `off`
 #define PANO_VEC(VT, base, off, width, n, site) \
     (*reinterpret_cast<VT*>(pano::checked_vec((base), (long long)(off), (width), (long long)(n), (site))))
@@ -78,6 +81,7 @@ __device__ __forceinline__ T* checked_vec(T* base, long long off, int width, lon
 #else
 #define PANO_AT(base, off, n, site) ((base)[off])
 #define PANO_IDX(i, n, site) (i)
+#define PANO_FLAG(cond, site) ((void)sizeof(cond))
 #define PANO_VEC(VT, base, off, width, n, site) (*reinterpret_cast<VT*>((base) + (off)))
 #define PANO_BOUNDS_READER(fn) \
     cudaError_t fn(unsigned*) { return cudaSuccess; }

@@ -9,17 +9,13 @@
 // Area3 (the limit as Lmin grows without bound), without Area2 0, with
 // neither 0.5.
 //
-// Distances are computed exactly, as integers, in two separable passes
-// (Felzenszwalb & Huttenlocher, "Distance transforms of sampled functions",
-// 2012):
+// Distances are computed exactly, as integers, in two separable passes:
 //   columns: g(x, y) = |y - y'| to the nearest feature pixel (x, y') of the
 //            same column, or "none";
 //   rows:    d2(x, y) = min over columns x' of (x - x')^2 + g(x', y)^2, the
-//            lower envelope of one parabola per column that has a feature.
-// The envelope of a row is built by one thread per area; the intersection
-// abscissae of neighbouring parabolas are rationals, compared exactly by
-// cross-multiplication in 64-bit integers, so d2 is exact. Only the final
-// ratio is rounded (FP32 square roots and one division).
+//            lower envelope of one parabola per column that has a feature
+//            (edt_row.cuh: banded envelopes merged in a tree).
+// Only the final ratio is rounded (FP32 square roots and one division).
 #include <stdio.h>
 #include <string.h>
 
@@ -28,142 +24,304 @@
 #include "bounds.cuh"
 #include "common.cuh"
 #include "ctx.h"
+#include "edt_row.cuh"
 #include "pano_flow.h"
 
 namespace pano {
 
 namespace {
 
-constexpr int kNone = 1 << 29;      // no feature pixel in the column
-constexpr int kColThreads = 128;
-constexpr int kRowThreads = 128;
+// ---------------------------------------------------------------------------
+// Column pass. A CTA of 32 x 32 threads owns 32 columns and walks down them
+// in blocks of 1024 rows; thread (tx, ty) holds rows ty*32 .. ty*32+31 of a
+// block of column tx as two 32-bit masks (Area1, Area2 pixels). A first pass
+// over the labels finds, per column and block, the first feature row; a
+// suffix minimum gives the first feature row at or after each block. The
+// second pass finds each row's nearest feature above and below from the
+// bits of its own mask, the masks of the other threads of its block (shared
+// memory), the last feature row of the blocks above and the first of the
+// blocks below. g of both areas is stored packed, Area1 in the low 16 bits:
+// one coalesced 4-byte store per pixel.
+// ---------------------------------------------------------------------------
+constexpr int kColW = 32;                     // columns per CTA
+constexpr int kColTY = 32;                    // threads along y, 32 rows each
+constexpr int kColBlock = 32 * kColTY;        // rows per block
+constexpr int kMaxBlocks = (65535 + kColBlock - 1) / kColBlock;
+constexpr int kAboveNone = -(1 << 20);        // y - kAboveNone > any distance
+constexpr int kBelowNone = INT_MAX;
 
-// Column pass: one thread per column, a downward and an upward sweep.
-__global__ void __launch_bounds__(kColThreads) edt_cols_kernel(const unsigned char* __restrict__ label, int h,
-                                                               int w, long long pitch, int* __restrict__ gL,
-                                                               int* __restrict__ gR) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x >= w) return;
+__device__ __forceinline__ void col_masks(const unsigned char* __restrict__ label, long long pitch, long long nl,
+                                          int h, int x, int y0, uint32_t* m1, uint32_t* m2) {
+    uint32_t a = 0, b = 0;
+    const int n = min(32, h - y0);
+    for (int i = 0; i < n; ++i) {
+        const unsigned char c = __ldg(&PANO_AT(label, (long long)(y0 + i) * pitch + x, nl, 501));
+        a |= (uint32_t)(c == 1) << i;
+        b |= (uint32_t)(c == 2) << i;
+    }
+    *m1 = a;
+    *m2 = b;
+}
+
+__global__ void __launch_bounds__(kColW * kColTY, 2) edt_cols_kernel(const unsigned char* __restrict__ label, int h,
+                                                                    int w, long long pitch, uint32_t* __restrict__ gq) {
+    __shared__ int s_next[2][kMaxBlocks + 1][kColW];  // first feature row at or after block rb's first row
+    __shared__ uint32_t s_mask[2][kColTY][kColW];
+    __shared__ int s_above[2][kColW];                 // last feature row above the current block
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kColW + tx;
+    const int x = blockIdx.x * kColW + tx;
+    const bool col_in = x < w;
+    const int nblk = (h + kColBlock - 1) / kColBlock;
     const long long nl = (long long)(h - 1) * pitch + w, ng = (long long)h * w;  // label and g elements
     (void)nl;
     (void)ng;
-    int dl = kNone, dr = kNone;
-    for (int y = 0; y < h; ++y) {
-        const unsigned char a = __ldg(&PANO_AT(label, (long long)y * pitch + x, nl, 501));
-        dl = a == 1 ? 0 : min(dl + 1, kNone);
-        dr = a == 2 ? 0 : min(dr + 1, kNone);
-        PANO_AT(gL, (long long)y * w + x, ng, 502) = dl;
-        PANO_AT(gR, (long long)y * w + x, ng, 502) = dr;
-    }
-    dl = dr = kNone;
-    for (int y = h - 1; y >= 0; --y) {
-        const unsigned char a = __ldg(&PANO_AT(label, (long long)y * pitch + x, nl, 503));
-        dl = a == 1 ? 0 : min(dl + 1, kNone);
-        dr = a == 2 ? 0 : min(dr + 1, kNone);
-        const long long o = (long long)y * w + x;
-        PANO_AT(gL, o, ng, 504) = min(PANO_AT(gL, o, ng, 504), dl);
-        PANO_AT(gR, o, ng, 504) = min(PANO_AT(gR, o, ng, 504), dr);
-    }
-}
-
-// Parabola of site q of a row of w columns: f(q) + (x - q)^2 with f = g^2.
-__device__ __forceinline__ long long site_f(const int* __restrict__ g, int w, int q) {
-    (void)w;
-    const long long v = PANO_AT(g, q, w, 505);
-    return v * v;
-}
-
-// Intersection abscissa of the parabolas of sites p < q as num / den (den > 0).
-__device__ __forceinline__ void intersect(const int* __restrict__ g, int w, int p, int q, long long* num,
-                                          long long* den) {
-    *num = (site_f(g, w, q) + (long long)q * q) - (site_f(g, w, p) + (long long)p * p);
-    *den = 2LL * (q - p);
-}
-
-// Lower envelope of one row: v[0..k] are the sites whose parabolas form it,
-// from left to right; returns k (-1 when the row has no site).
-__device__ int build_envelope(const int* __restrict__ g, int w, int* __restrict__ v) {
-    int k = -1;
-    for (int q = 0; q < w; ++q) {
-        if (PANO_AT(g, q, w, 506) >= kNone) continue;
-        if (k < 0) {
-            PANO_AT(v, ++k, w, 507) = q;
-            continue;
-        }
-        // drop envelope parabolas that the new one hides: while the new
-        // intersection lies at or left of the start of the last parabola
-        while (k >= 1) {
-            long long n1, d1, n0, d0;
-            intersect(g, w, PANO_AT(v, k, w, 508), q, &n1, &d1);  // s(v[k], q)
-            intersect(g, w, PANO_AT(v, k - 1, w, 508), PANO_AT(v, k, w, 508), &n0, &d0);  // z[k] = s(v[k-1], v[k])
-            if (n1 * d0 <= n0 * d1) --k;
-            else break;
-        }
-        PANO_AT(v, ++k, w, 507) = q;
-    }
-    return k;
-}
-
-// Squared distance at column x from an envelope of k + 1 sites.
-__device__ __forceinline__ long long envelope_at(const int* __restrict__ g, const int* __restrict__ v, int w, int k,
-                                                int x) {
-    // largest j with z[j] <= x, z[0] = -infinity, z[j] = s(v[j-1], v[j])
-    int lo = 0, hi = k;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        long long n, d;
-        intersect(g, w, PANO_AT(v, mid - 1, w, 509), PANO_AT(v, mid, w, 509), &n, &d);
-        if (n <= (long long)x * d) lo = mid;
-        else hi = mid - 1;
-    }
-    const int q = PANO_AT(v, lo, w, 509);
-    const long long dx = x - q;
-    return dx * dx + site_f(g, w, q);
-}
-
-// Row pass and Eq. (1): one CTA per row. Warp 0 builds the Area1 envelope,
-// warp 1 the Area2 envelope (one thread each); then every thread fills
-// columns.
-__global__ void __launch_bounds__(kRowThreads) edt_rows_blend_kernel(const unsigned char* __restrict__ label, int h,
-                                                                     int w, long long pitch,
-                                                                     const int* __restrict__ gL,
-                                                                     const int* __restrict__ gR,
-                                                                     float* __restrict__ blend, int blend_pitch) {
-    // dynamic shared memory only (the kernel's limit is set to the device
-    // maximum): the two envelope sizes, then the sites of each envelope
-    extern __shared__ int s_dyn[];
-    int* s_k = s_dyn;
-    int* vL = s_dyn + 2;
-    int* vR = vL + w;
-    const int y = blockIdx.x;
-    const int* rowL = gL + (long long)y * w;
-    const int* rowR = gR + (long long)y * w;
-    if (threadIdx.x == 0) s_k[0] = build_envelope(rowL, w, vL);
-    if (threadIdx.x == 32) s_k[1] = build_envelope(rowR, w, vR);
+    constexpr int NN = 2 * (kMaxBlocks + 1) * kColW;
+    for (int i = tid; i < NN; i += kColW * kColTY) PANO_AT(&s_next[0][0][0], i, NN, 502) = kBelowNone;
+    if (tid < 2 * kColW) PANO_AT(&s_above[0][0], tid, 2 * kColW, 503) = kAboveNone;
     __syncthreads();
-    const int kL = s_k[0], kR = s_k[1];
+    for (int rb = 0; rb < nblk; ++rb) {
+        const int y0 = rb * kColBlock + ty * 32;
+        uint32_t m1 = 0, m2 = 0;
+        if (col_in && y0 < h) col_masks(label, pitch, nl, h, x, y0, &m1, &m2);
+        if (m1) atomicMin(&s_next[0][rb][tx], y0 + __ffs(m1) - 1);
+        if (m2) atomicMin(&s_next[1][rb][tx], y0 + __ffs(m2) - 1);
+    }
+    __syncthreads();
+    if (ty < 2)
+        for (int rb = nblk - 1; rb >= 0; --rb) s_next[ty][rb][tx] = min(s_next[ty][rb][tx], s_next[ty][rb + 1][tx]);
+    __syncthreads();
+    for (int rb = 0; rb < nblk; ++rb) {
+        const int yb = rb * kColBlock, y0 = yb + ty * 32;
+        uint32_t m[2] = {0, 0};
+        if (col_in && y0 < h) col_masks(label, pitch, nl, h, x, y0, &m[0], &m[1]);
+        s_mask[0][ty][tx] = m[0];
+        s_mask[1][ty][tx] = m[1];
+        __syncthreads();
+        int above[2], below[2];  // nearest feature rows above and below this thread's 32 rows
+#pragma unroll
+        for (int a = 0; a < 2; ++a) {
+            int p = s_above[a][tx];
+            for (int k = ty - 1; k >= 0; --k) {
+                const uint32_t v = s_mask[a][k][tx];
+                if (v) {
+                    p = yb + k * 32 + 31 - __clz(v);
+                    break;
+                }
+            }
+            int n = s_next[a][rb + 1][tx];
+            for (int k = ty + 1; k < kColTY; ++k) {
+                const uint32_t v = s_mask[a][k][tx];
+                if (v) {
+                    n = yb + k * 32 + __ffs(v) - 1;
+                    break;
+                }
+            }
+            above[a] = p;
+            below[a] = n;
+        }
+        if (col_in && y0 < h) {
+            const int n = min(32, h - y0);
+            for (int i = 0; i < n; ++i) {
+                const int yy = y0 + i;
+                uint32_t packed = 0;
+#pragma unroll
+                for (int a = 0; a < 2; ++a) {
+                    const uint32_t up = m[a] & (0xFFFFFFFFu >> (31 - i));  // rows y0 .. yy
+                    const uint32_t dn = m[a] & (0xFFFFFFFFu << i);         // rows yy .. y0 + 31
+                    const int ab = up ? y0 + 31 - __clz(up) : above[a];
+                    const int be = dn ? y0 + __ffs(dn) - 1 : below[a];
+                    const long long d = min((long long)yy - ab, (long long)be - yy);
+                    packed |= (d >= (long long)edt::kNoSite ? edt::kNoSite : (uint32_t)d) << (16 * a);
+                }
+                PANO_AT(gq, (long long)yy * w + x, ng, 504) = packed;
+            }
+        }
+        __syncthreads();  // the masks and s_above are read
+        if (ty == kColTY - 1) {
+            s_above[0][tx] = m[0] ? y0 + 31 - __clz(m[0]) : above[0];
+            s_above[1][tx] = m[1] ? y0 + 31 - __clz(m[1]) : above[1];
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Row pass and Eq. (1): one CTA of kRowThreads per row, one band of
+// ceil(w / kRowThreads) columns per thread (edt_row.cuh for the steps).
+// Shared memory, all dynamic (the kernel's limit is set to the device
+// maximum): the packed g row (4 B per column), the kept sites of both areas
+// (2 x 2 B per column), five arrays of two ints per band and 34 ints for the
+// scans.
+// ---------------------------------------------------------------------------
+constexpr int kRowThreads = 512;
+constexpr int kRowWarps = kRowThreads / 32;
+
+// inclusive prefix maximum over the threads of the block
+__device__ __forceinline__ int block_prefix_max(int v, int* s_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v = max(v, t);
+    }
+    if (lane == 31) s_warp[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < kRowWarps ? s_warp[lane] : INT_MIN;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t = max(t, u);
+        }
+        if (lane < kRowWarps) s_warp[lane] = t;
+    }
+    __syncthreads();
+    if (wid > 0) v = max(v, s_warp[wid - 1]);
+    __syncthreads();
+    return v;
+}
+
+// inclusive suffix minimum over the threads of the block
+__device__ __forceinline__ int block_suffix_min(int v, int* s_warp) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_down_sync(0xffffffffu, v, o);
+        if (lane + o < 32) v = min(v, t);
+    }
+    if (lane == 0) s_warp[wid] = v;
+    __syncthreads();
+    if (wid == 0) {
+        int t = lane < kRowWarps ? s_warp[lane] : INT_MAX;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_down_sync(0xffffffffu, t, o);
+            if (lane + o < 32) t = min(t, u);
+        }
+        if (lane < kRowWarps) s_warp[lane] = t;
+    }
+    __syncthreads();
+    if (wid + 1 < kRowWarps) v = min(v, s_warp[wid + 1]);
+    __syncthreads();
+    return v;
+}
+
+__global__ void __launch_bounds__(kRowThreads, 2) edt_rows_blend_kernel(const unsigned char* __restrict__ label, int h,
+                                                                       int w, long long pitch,
+                                                                       const uint32_t* __restrict__ gq,
+                                                                       float* __restrict__ blend, int blend_pitch) {
+    using namespace edt;
+    constexpr int NB = kRowThreads;
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint32_t* gs = reinterpret_cast<uint32_t*>(s_dyn);                     // [w]
+    uint16_t* st = reinterpret_cast<uint16_t*>(s_dyn + 4 * (size_t)w);     // [2][w]
+    int* lo = reinterpret_cast<int*>(s_dyn + 8 * (size_t)w);               // [2][NB]
+    int* hi = lo + 2 * NB;                                                 // [2][NB]
+    int* gfirst = hi + 2 * NB;  // [2][NB] first band of a group; then the last band <= b with a site
+    int* glast = gfirst + 2 * NB;  // [2][NB] last band of a group; then the first band >= b with a site
+    int* zs = glast + 2 * NB;      // [2][NB] start of the region of band b's first site
+    int* s_warp = zs + 2 * NB;     // [32] warp totals of the scans
+    int* s_any = s_warp + 32;      // [2] the row has sites of Area1 / Area2
+    const int tid = threadIdx.x, y = blockIdx.x;
+    (void)h;
+    const int bw = (w + NB - 1) / NB;
+    const long long ng = (long long)h * w;
+    (void)ng;
+    for (int i = tid; i < w; i += NB) PANO_AT(gs, i, w, 505) = PANO_AT(gq, (long long)y * w + i, ng, 506);
+    __syncthreads();
+    const int x0 = min(w, tid * bw), x1 = min(w, x0 + bw);
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int k = band_envelope(gs, st + a * w, w, a, x0, x1);
+        PANO_AT(lo, a * NB + tid, 2 * NB, 507) = x0;
+        PANO_AT(hi, a * NB + tid, 2 * NB, 507) = x0 + k;
+        PANO_AT(gfirst, a * NB + tid, 2 * NB, 507) = k ? tid : -1;
+        PANO_AT(glast, a * NB + tid, 2 * NB, 507) = k ? tid : -1;
+    }
+    __syncthreads();
+    // merge tree: in the round of stride s, thread lg (a multiple of 2 s)
+    // merges the groups lg and lg + s of Area1, thread lg + 1 those of Area2
+    for (int s = 1; s < NB; s <<= 1) {
+        const int a = tid & 1, lg = tid - a;
+        if ((lg & (2 * s - 1)) == 0 && lg + s < NB) {
+            int* GF = gfirst + a * NB;
+            int* GL = glast + a * NB;
+            const int lf = PANO_AT(GF, lg, NB, 508), ll = PANO_AT(GL, lg, NB, 508);
+            const int rf = PANO_AT(GF, lg + s, NB, 508), rl = PANO_AT(GL, lg + s, NB, 508);
+            if (rf >= 0) {
+                if (lf < 0) {
+                    GF[lg] = rf;
+                } else {
+                    const bool ok = merge_groups(gs, st + a * w, lo + a * NB, hi + a * NB, w, NB, a, lf, ll, rf, rl);
+                    PANO_FLAG(!ok, 509);  // the merge reached its iteration limit
+                    (void)ok;
+                }
+                GL[lg] = rl;
+            }
+        }
+        __syncthreads();
+    }
+    if (tid < 2) s_any[tid] = gfirst[tid * NB] >= 0;
+    // the last band <= b and the first band >= b that keep a site
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const bool kept = hi[a * NB + tid] > lo[a * NB + tid];
+        const int pv = block_prefix_max(kept ? tid : -1, s_warp);
+        const int nx = block_suffix_min(kept ? tid : NB, s_warp);
+        gfirst[a * NB + tid] = pv;
+        glast[a * NB + tid] = nx;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int o = a * NB;
+        if (hi[o + tid] > lo[o + tid]) {
+            const int pb = tid > 0 ? gfirst[o + tid - 1] : -1;
+            int z = -1;
+            if (pb >= 0) {
+                const int p = PANO_AT(st + a * w, hi[o + pb] - 1, w, 510), q = PANO_AT(st + a * w, lo[o + tid], w, 510);
+                z = region_start(f_of(gs, w, a, p), p, f_of(gs, w, a, q), q, w);
+            }
+            zs[o + tid] = z;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 2; ++a) {
+        const int o = a * NB;
+        if (hi[o + tid] <= lo[o + tid]) {
+            const int n = glast[o + tid];
+            zs[o + tid] = n < NB ? PANO_AT(zs, o + n, 2 * NB, 511) : w;
+        }
+    }
+    __syncthreads();
+    if (x0 >= x1) return;
+    const bool any1 = s_any[0] != 0, any2 = s_any[1] != 0;
+    Walker k1 = {0, 0}, k2 = {0, 0};
+    if (any1) k1 = walk_start(gs, st, lo, hi, zs, w, NB, 0, x0);
+    if (any2) k2 = walk_start(gs, st + w, lo + NB, hi + NB, zs + NB, w, NB, 1, x0);
     const unsigned char* lab = label + (long long)y * pitch;
     float* out = blend + (long long)y * blend_pitch;
-    for (int x = threadIdx.x; x < w; x += blockDim.x) {
-        const unsigned char a = PANO_AT(lab, x, w, 510);
+    for (int x = x0; x < x1; ++x) {
+        const unsigned char c = PANO_AT(lab, x, w, 512);
         float b;
-        if (a == 1) {
+        if (c == 1) {
             b = 0.f;
-        } else if (a == 2) {
+        } else if (c == 2) {
             b = 1.f;
-        } else if (a == 3) {
-            if (kL < 0 && kR < 0) b = 0.5f;
-            else if (kL < 0) b = 1.f;
-            else if (kR < 0) b = 0.f;
+        } else if (c == 3) {
+            if (!any1 && !any2) b = 0.5f;
+            else if (!any1) b = 1.f;
+            else if (!any2) b = 0.f;
             else {
-                const float dl = sqrtf((float)envelope_at(rowL, vL, w, kL, x));
-                const float dr = sqrtf((float)envelope_at(rowR, vR, w, kR, x));
+                const float dl = sqrtf((float)walk_to(gs, st, lo, hi, glast, w, NB, 0, x, &k1));
+                const float dr = sqrtf((float)walk_to(gs, st + w, lo + NB, hi + NB, glast + NB, w, NB, 1, x, &k2));
                 b = dl / (dl + dr);
             }
         } else {
             b = 0.5f;
         }
-        PANO_AT(out, x, w, 511) = b;
+        PANO_AT(out, x, w, 513) = b;
     }
 }
 
@@ -171,9 +329,9 @@ __global__ void __launch_bounds__(kRowThreads) edt_rows_blend_kernel(const unsig
 
 PANO_BOUNDS_READER(bounds_read_edt)
 
-size_t blend_coeff_scratch_bytes(int h, int w) { return (size_t)2 * h * w * sizeof(int); }
+size_t blend_coeff_scratch_bytes(int h, int w) { return (size_t)h * w * sizeof(uint32_t); }
 
-size_t blend_coeff_row_smem(int w) { return (size_t)(2 * w + 2) * sizeof(int); }
+size_t blend_coeff_row_smem(int w) { return (size_t)8 * w + (size_t)(5 * 2 * kRowThreads + 34) * sizeof(int); }
 
 cudaError_t blend_coeff_prepare(int max_smem_bytes) {
     return cudaFuncSetAttribute(edt_rows_blend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
@@ -181,12 +339,11 @@ cudaError_t blend_coeff_prepare(int max_smem_bytes) {
 
 cudaError_t launch_blend_coeff(const unsigned char* label, int h, int w, long long pitch, float* blend,
                                int blend_pitch, void* scratch, cudaStream_t s) {
-    int* gL = static_cast<int*>(scratch);
-    int* gR = gL + (size_t)h * w;
-    edt_cols_kernel<<<(w + kColThreads - 1) / kColThreads, kColThreads, 0, s>>>(label, h, w, pitch, gL, gR);
+    uint32_t* gq = static_cast<uint32_t*>(scratch);
+    edt_cols_kernel<<<(w + kColW - 1) / kColW, dim3(kColW, kColTY), 0, s>>>(label, h, w, pitch, gq);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    edt_rows_blend_kernel<<<h, kRowThreads, blend_coeff_row_smem(w), s>>>(label, h, w, pitch, gL, gR, blend,
+    edt_rows_blend_kernel<<<h, kRowThreads, blend_coeff_row_smem(w), s>>>(label, h, w, pitch, gq, blend,
                                                                           blend_pitch);
     return cudaGetLastError();
 }
@@ -207,7 +364,7 @@ pano_status pano_blend_coeff(const unsigned char* label, int h, int w, size_t la
     if (!label || !blend || !scratch) return fail(PANO_ERR_INVALID_ARG, "label, blend or scratch is NULL");
     if (h < 1 || w < 1) return fail(PANO_ERR_INVALID_ARG, "canvas size %dx%d", h, w);
     if (h > 65535 || w > 65535)
-        return fail(PANO_ERR_UNSUPPORTED, "canvas %dx%d: sides above 65535 (64-bit envelope products)", h, w);
+        return fail(PANO_ERR_UNSUPPORTED, "canvas %dx%d: sides above 65535 (16-bit distances and columns)", h, w);
     if (label_pitch < (size_t)w) return fail(PANO_ERR_INVALID_ARG, "label_pitch %zu < w %d", label_pitch, w);
     if (blend_pitch < w) return fail(PANO_ERR_INVALID_ARG, "blend_pitch %d < w %d", blend_pitch, w);
     if (((uintptr_t)blend) % 4 || ((uintptr_t)scratch) % 4)

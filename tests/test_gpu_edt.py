@@ -116,6 +116,56 @@ def test_full_canvas_at_sampled_pixels():
     assert np.isfinite(got).all() and (got >= 0).all() and (got <= 1).all()
 
 
+def _sampled(label, n, seed):
+    """GPU Blend against the oracle's brute force at n pixels (Area3 first)."""
+    got = gpu_blend(label)
+    g = np.random.default_rng(seed)
+    area3 = np.argwhere(label == 3)
+    pick = area3[g.choice(len(area3), min(n, len(area3)), replace=False)]
+    other = np.stack([g.integers(0, label.shape[0], n // 4), g.integers(0, label.shape[1], n // 4)], -1)
+    ys, xs = np.concatenate([pick[:, 0], other[:, 0]]), np.concatenate([pick[:, 1], other[:, 1]])
+    np.testing.assert_allclose(got[ys, xs], oracle.blend_coeff_at(label, ys, xs), rtol=0, atol=TOL)
+    assert np.isfinite(got).all() and (got >= 0).all() and (got <= 1).all()
+
+
+def test_wide_canvas_many_columns_per_band():
+    """26000 columns (51 per thread of the row pass, near the shared-memory
+    limit), wavy seams, holes and scattered Area1/Area2 pixels."""
+    label = overlap_canvas(24, 26000, 10)
+    g = np.random.default_rng(11)
+    label[g.integers(0, 24, 300), g.integers(0, 26000, 300)] = g.choice([1, 2], 300)
+    _sampled(label, 400, 12)
+
+
+def test_tall_canvas_carries_across_row_blocks():
+    """5000 rows (five 1024-row blocks of the column pass): the nearest
+    feature of a column often lies blocks away."""
+    h, w = 5000, 37
+    label = np.full((h, w), 3, np.uint8)
+    g = np.random.default_rng(13)
+    for x in range(w):                       # a few feature pixels per column, anywhere
+        k = g.integers(0, 4)
+        label[g.integers(0, h, k), x] = g.choice([1, 2], k)
+    label[:, 5] = 3                          # columns without any feature pixel
+    label[1023:1026, 7] = 1                  # features at block edges
+    label[2047, 9], label[2048, 9] = 2, 1
+    _sampled(label, 1500, 14)
+
+
+@pytest.mark.parametrize("shape,seed", [((90, 1100), 15), ((33, 4097), 16)])
+def test_dense_random_labels_sampled(shape, seed):
+    g = np.random.default_rng(seed)
+    label = g.choice([0, 1, 2, 3], p=[0.1, 0.15, 0.15, 0.6], size=shape).astype(np.uint8)
+    _sampled(label, 1500, seed + 100)
+
+
+def test_too_wide_canvas_is_refused():
+    lab = torch.full((2, 27000), 3, dtype=torch.uint8, device=DEV)
+    with pytest.raises(binding.PanoError) as e:
+        binding.blend_coeff(lab)
+    assert e.value.status == binding.PANO_ERR_UNSUPPORTED
+
+
 def test_bad_arguments_raise():
     lab = torch.zeros((8, 8), dtype=torch.uint8, device=DEV)
     with pytest.raises(binding.PanoError):
