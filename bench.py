@@ -635,7 +635,7 @@ def run_blend_coeff(args):
                        "area3_fraction": float((lab == 3).mean())},
             "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None,
-                         "kernel": "edt_cols_kernel + edt_rows_blend_kernel", "alg_bytes_per_launch": alg,
+                         "kernel": "edt_cols_kernel + edt_row_kernel (Area1) + edt_row_kernel (Area2)", "alg_bytes_per_launch": alg,
                          "peak_source": f"{src} hbm_gbs"}}
     print(json.dumps(line), flush=True)
     return 0

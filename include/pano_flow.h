@@ -189,9 +189,9 @@ PANO_API const char* pano_last_error(const pano_flow_ctx* ctx);
  * distance transform); the ratio is rounded in FP32. The Blend array of a
  * strip can be passed to pano_blend_pair.
  * scratch: device memory of at least pano_blend_coeff_scratch_bytes(h, w)
- * bytes (4 * h * w), 4-byte aligned; label, blend and scratch must not
+ * bytes (8 * h * w), 4-byte aligned; label, blend and scratch must not
  * overlap. Sides up to 65535; the width is limited further by shared memory
- * (8 bytes per column and 20 KB per row: 26000 columns on a GB300).
+ * (4 bytes per column and 5 KB per row: 56000 columns on a GB300).
  * Errors: INVALID_ARG, UNSUPPORTED, CUDA.
  * ---------------------------------------------------------------------- */
 PANO_API size_t pano_blend_coeff_scratch_bytes(int h, int w);

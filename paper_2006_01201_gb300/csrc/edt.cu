@@ -40,8 +40,8 @@ namespace {
 // second pass finds each row's nearest feature above and below from the
 // bits of its own mask, the masks of the other threads of its block (shared
 // memory), the last feature row of the blocks above and the first of the
-// blocks below. g of both areas is stored packed, Area1 in the low 16 bits:
-// one coalesced 4-byte store per pixel.
+// blocks below. g of each area goes to a plane of 16-bit values (coalesced
+// 2-byte stores; edt::kNoSite where the column has no feature pixel).
 // ---------------------------------------------------------------------------
 constexpr int kColW = 32;                     // columns per CTA
 constexpr int kColTY = 32;                    // threads along y, 32 rows each
@@ -64,7 +64,8 @@ __device__ __forceinline__ void col_masks(const unsigned char* __restrict__ labe
 }
 
 __global__ void __launch_bounds__(kColW * kColTY, 2) edt_cols_kernel(const unsigned char* __restrict__ label, int h,
-                                                                    int w, long long pitch, uint32_t* __restrict__ gq) {
+                                                                    int w, long long pitch, uint16_t* __restrict__ g1,
+                                                                    uint16_t* __restrict__ g2) {
     __shared__ int s_next[2][kMaxBlocks + 1][kColW];  // first feature row at or after block rb's first row
     __shared__ uint32_t s_mask[2][kColTY][kColW];
     __shared__ int s_above[2][kColW];                 // last feature row above the current block
@@ -123,7 +124,7 @@ __global__ void __launch_bounds__(kColW * kColTY, 2) edt_cols_kernel(const unsig
             const int n = min(32, h - y0);
             for (int i = 0; i < n; ++i) {
                 const int yy = y0 + i;
-                uint32_t packed = 0;
+                uint32_t g[2];
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
                     const uint32_t up = m[a] & (0xFFFFFFFFu >> (31 - i));  // rows y0 .. yy
@@ -131,9 +132,10 @@ __global__ void __launch_bounds__(kColW * kColTY, 2) edt_cols_kernel(const unsig
                     const int ab = up ? y0 + 31 - __clz(up) : above[a];
                     const int be = dn ? y0 + __ffs(dn) - 1 : below[a];
                     const long long d = min((long long)yy - ab, (long long)be - yy);
-                    packed |= (d >= (long long)edt::kNoSite ? edt::kNoSite : (uint32_t)d) << (16 * a);
+                    g[a] = d >= (long long)edt::kNoSite ? edt::kNoSite : (uint32_t)d;
                 }
-                PANO_AT(gq, (long long)yy * w + x, ng, 504) = packed;
+                PANO_AT(g1, (long long)yy * w + x, ng, 504) = (uint16_t)g[0];
+                PANO_AT(g2, (long long)yy * w + x, ng, 504) = (uint16_t)g[1];
             }
         }
         __syncthreads();  // the masks and s_above are read
@@ -146,15 +148,20 @@ __global__ void __launch_bounds__(kColW * kColTY, 2) edt_cols_kernel(const unsig
 }
 
 // ---------------------------------------------------------------------------
-// Row pass and Eq. (1): one CTA of kRowThreads per row, one band of
+// Row pass: one CTA of kRowThreads per row and area, one band of
 // ceil(w / kRowThreads) columns per thread (edt_row.cuh for the steps).
+// The Area1 launch writes the distances to Area1 (FP32 square roots of the
+// exact squared distances, +inf with no Area1 pixel on the canvas) of the
+// Area3 pixels to a plane; the Area2 launch reads them there and writes
+// Eq. (1).
 // Shared memory, all dynamic (the kernel's limit is set to the device
-// maximum): the packed g row (4 B per column), the kept sites of both areas
-// (2 x 2 B per column), five arrays of two ints per band and 34 ints for the
-// scans.
+// maximum): the row's g (2 B per column), the kept sites (2 B per column),
+// five ints per band and 33 ints for the scans; five CTAs fit on an SM at
+// 9000 columns.
 // ---------------------------------------------------------------------------
-constexpr int kRowThreads = 512;
+constexpr int kRowThreads = 256;
 constexpr int kRowWarps = kRowThreads / 32;
+constexpr int kRowCtas = 5;
 
 // inclusive prefix maximum over the threads of the block
 __device__ __forceinline__ int block_prefix_max(int v, int* s_warp) {
@@ -206,122 +213,119 @@ __device__ __forceinline__ int block_suffix_min(int v, int* s_warp) {
     return v;
 }
 
-__global__ void __launch_bounds__(kRowThreads, 2) edt_rows_blend_kernel(const unsigned char* __restrict__ label, int h,
-                                                                       int w, long long pitch,
-                                                                       const uint32_t* __restrict__ gq,
-                                                                       float* __restrict__ blend, int blend_pitch) {
+// kFinal false: Area1 (g = g1), writes dist1; true: Area2, writes Blend
+template <bool kFinal>
+__global__ void __launch_bounds__(kRowThreads, kRowCtas) edt_row_kernel(const unsigned char* __restrict__ label,
+                                                                        int h, int w, long long pitch,
+                                                                        const uint16_t* __restrict__ gplane,
+                                                                        float* __restrict__ dist1,
+                                                                        float* __restrict__ blend, int blend_pitch) {
     using namespace edt;
     constexpr int NB = kRowThreads;
     extern __shared__ __align__(16) unsigned char s_dyn[];
-    uint32_t* gs = reinterpret_cast<uint32_t*>(s_dyn);                     // [w]
-    uint16_t* st = reinterpret_cast<uint16_t*>(s_dyn + 4 * (size_t)w);     // [2][w]
-    int* lo = reinterpret_cast<int*>(s_dyn + 8 * (size_t)w);               // [2][NB]
-    int* hi = lo + 2 * NB;                                                 // [2][NB]
-    int* gfirst = hi + 2 * NB;  // [2][NB] first band of a group; then the last band <= b with a site
-    int* glast = gfirst + 2 * NB;  // [2][NB] last band of a group; then the first band >= b with a site
-    int* zs = glast + 2 * NB;      // [2][NB] start of the region of band b's first site
-    int* s_warp = zs + 2 * NB;     // [32] warp totals of the scans
-    int* s_any = s_warp + 32;      // [2] the row has sites of Area1 / Area2
+    uint16_t* gs = reinterpret_cast<uint16_t*>(s_dyn);                  // [w]
+    uint16_t* st = gs + w;                                              // [w]
+    int* lo = reinterpret_cast<int*>(s_dyn + 4 * (size_t)w);            // [NB]
+    int* hi = lo + NB;                                                  // [NB]
+    int* gfirst = hi + NB;   // [NB] first band of a group; then the last band <= b with a site
+    int* glast = gfirst + NB;  // [NB] last band of a group; then the first band >= b with a site
+    int* zs = glast + NB;      // [NB] start of the region of band b's first site
+    int* s_warp = zs + NB;     // [32] warp totals of the scans
+    int* s_any = s_warp + 32;  // [1] the row has a site
     const int tid = threadIdx.x, y = blockIdx.x;
-    (void)h;
     const int bw = (w + NB - 1) / NB;
     const long long ng = (long long)h * w;
     (void)ng;
-    for (int i = tid; i < w; i += NB) PANO_AT(gs, i, w, 505) = PANO_AT(gq, (long long)y * w + i, ng, 506);
+    for (int i = tid; i < w; i += NB) PANO_AT(gs, i, w, 505) = PANO_AT(gplane, (long long)y * w + i, ng, 506);
     __syncthreads();
     const int x0 = min(w, tid * bw), x1 = min(w, x0 + bw);
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int k = band_envelope(gs, st + a * w, w, a, x0, x1);
-        PANO_AT(lo, a * NB + tid, 2 * NB, 507) = x0;
-        PANO_AT(hi, a * NB + tid, 2 * NB, 507) = x0 + k;
-        PANO_AT(gfirst, a * NB + tid, 2 * NB, 507) = k ? tid : -1;
-        PANO_AT(glast, a * NB + tid, 2 * NB, 507) = k ? tid : -1;
+    {
+        const int k = band_envelope(gs, st, w, x0, x1);
+        PANO_AT(lo, tid, NB, 507) = x0;
+        PANO_AT(hi, tid, NB, 507) = x0 + k;
+        PANO_AT(gfirst, tid, NB, 507) = k ? tid : -1;
+        PANO_AT(glast, tid, NB, 507) = k ? tid : -1;
     }
     __syncthreads();
     // merge tree: in the round of stride s, thread lg (a multiple of 2 s)
-    // merges the groups lg and lg + s of Area1, thread lg + 1 those of Area2
+    // merges the groups lg and lg + s
     for (int s = 1; s < NB; s <<= 1) {
-        const int a = tid & 1, lg = tid - a;
+        const int lg = tid;
         if ((lg & (2 * s - 1)) == 0 && lg + s < NB) {
-            int* GF = gfirst + a * NB;
-            int* GL = glast + a * NB;
-            const int lf = PANO_AT(GF, lg, NB, 508), ll = PANO_AT(GL, lg, NB, 508);
-            const int rf = PANO_AT(GF, lg + s, NB, 508), rl = PANO_AT(GL, lg + s, NB, 508);
+            const int lf = PANO_AT(gfirst, lg, NB, 508), ll = PANO_AT(glast, lg, NB, 508);
+            const int rf = PANO_AT(gfirst, lg + s, NB, 508), rl = PANO_AT(glast, lg + s, NB, 508);
             if (rf >= 0) {
                 if (lf < 0) {
-                    GF[lg] = rf;
+                    gfirst[lg] = rf;
                 } else {
-                    const bool ok = merge_groups(gs, st + a * w, lo + a * NB, hi + a * NB, w, NB, a, lf, ll, rf, rl);
+                    const bool ok = merge_groups(gs, st, lo, hi, w, NB, lf, ll, rf, rl);
                     PANO_FLAG(!ok, 509);  // the merge reached its iteration limit
                     (void)ok;
                 }
-                GL[lg] = rl;
+                glast[lg] = rl;
             }
         }
         __syncthreads();
     }
-    if (tid < 2) s_any[tid] = gfirst[tid * NB] >= 0;
+    if (tid == 0) s_any[0] = gfirst[0] >= 0;
     // the last band <= b and the first band >= b that keep a site
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const bool kept = hi[a * NB + tid] > lo[a * NB + tid];
+    {
+        const bool kept = hi[tid] > lo[tid];
         const int pv = block_prefix_max(kept ? tid : -1, s_warp);
         const int nx = block_suffix_min(kept ? tid : NB, s_warp);
-        gfirst[a * NB + tid] = pv;
-        glast[a * NB + tid] = nx;
+        gfirst[tid] = pv;
+        glast[tid] = nx;
     }
     __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int o = a * NB;
-        if (hi[o + tid] > lo[o + tid]) {
-            const int pb = tid > 0 ? gfirst[o + tid - 1] : -1;
-            int z = -1;
-            if (pb >= 0) {
-                const int p = PANO_AT(st + a * w, hi[o + pb] - 1, w, 510), q = PANO_AT(st + a * w, lo[o + tid], w, 510);
-                z = region_start(f_of(gs, w, a, p), p, f_of(gs, w, a, q), q, w);
-            }
-            zs[o + tid] = z;
+    if (hi[tid] > lo[tid]) {
+        const int pb = tid > 0 ? gfirst[tid - 1] : -1;
+        int z = -1;
+        if (pb >= 0) {
+            const int p = PANO_AT(st, hi[pb] - 1, w, 510), q = PANO_AT(st, lo[tid], w, 510);
+            z = region_start(f_of(gs, w, p), p, f_of(gs, w, q), q, w);
         }
+        zs[tid] = z;
     }
     __syncthreads();
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-        const int o = a * NB;
-        if (hi[o + tid] <= lo[o + tid]) {
-            const int n = glast[o + tid];
-            zs[o + tid] = n < NB ? PANO_AT(zs, o + n, 2 * NB, 511) : w;
-        }
+    if (hi[tid] <= lo[tid]) {
+        const int n = glast[tid];
+        zs[tid] = n < NB ? PANO_AT(zs, n, NB, 511) : w;
     }
     __syncthreads();
     if (x0 >= x1) return;
-    const bool any1 = s_any[0] != 0, any2 = s_any[1] != 0;
-    Walker k1 = {0, 0}, k2 = {0, 0};
-    if (any1) k1 = walk_start(gs, st, lo, hi, zs, w, NB, 0, x0);
-    if (any2) k2 = walk_start(gs, st + w, lo + NB, hi + NB, zs + NB, w, NB, 1, x0);
+    const bool any = s_any[0] != 0;
+    Walker k = {0, 0, 0, 0, 0};
+    if (any) k = walk_start(gs, st, lo, hi, zs, w, NB, x0);
+    const long long ro = (long long)y * w;
     const unsigned char* lab = label + (long long)y * pitch;
-    float* out = blend + (long long)y * blend_pitch;
-    for (int x = x0; x < x1; ++x) {
-        const unsigned char c = PANO_AT(lab, x, w, 512);
-        float b;
-        if (c == 1) {
-            b = 0.f;
-        } else if (c == 2) {
-            b = 1.f;
-        } else if (c == 3) {
-            if (!any1 && !any2) b = 0.5f;
-            else if (!any1) b = 1.f;
-            else if (!any2) b = 0.f;
-            else {
-                const float dl = sqrtf((float)walk_to(gs, st, lo, hi, glast, w, NB, 0, x, &k1));
-                const float dr = sqrtf((float)walk_to(gs, st + w, lo + NB, hi + NB, glast + NB, w, NB, 1, x, &k2));
-                b = dl / (dl + dr);
+    if constexpr (!kFinal) {
+        // only Area3 pixels read the distances to Area1
+        for (int x = x0; x < x1; ++x)
+            if (PANO_AT(lab, x, w, 512) == 3)
+                PANO_AT(dist1, ro + x, ng, 512) =
+                    any ? sqrtf((float)walk_to(gs, st, lo, hi, glast, w, NB, x, &k)) : INFINITY;
+    } else {
+        float* out = blend + (long long)y * blend_pitch;
+        for (int x = x0; x < x1; ++x) {
+            const unsigned char c = PANO_AT(lab, x, w, 513);
+            float b;
+            if (c == 1) {
+                b = 0.f;
+            } else if (c == 2) {
+                b = 1.f;
+            } else if (c == 3) {
+                const float dl = PANO_AT(dist1, ro + x, ng, 514);
+                const float dr = any ? sqrtf((float)walk_to(gs, st, lo, hi, glast, w, NB, x, &k)) : INFINITY;
+                const bool no1 = isinf(dl), no2 = !any;
+                if (no1 && no2) b = 0.5f;
+                else if (no1) b = 1.f;
+                else if (no2) b = 0.f;
+                else b = dl / (dl + dr);
+            } else {
+                b = 0.5f;
             }
-        } else {
-            b = 0.5f;
+            PANO_AT(out, x, w, 515) = b;
         }
-        PANO_AT(out, x, w, 513) = b;
     }
 }
 
@@ -329,22 +333,31 @@ __global__ void __launch_bounds__(kRowThreads, 2) edt_rows_blend_kernel(const un
 
 PANO_BOUNDS_READER(bounds_read_edt)
 
-size_t blend_coeff_scratch_bytes(int h, int w) { return (size_t)h * w * sizeof(uint32_t); }
+size_t blend_coeff_scratch_bytes(int h, int w) {
+    return (size_t)h * w * (2 * sizeof(uint16_t) + sizeof(float));  // g of both areas, distances to Area1
+}
 
-size_t blend_coeff_row_smem(int w) { return (size_t)8 * w + (size_t)(5 * 2 * kRowThreads + 34) * sizeof(int); }
+size_t blend_coeff_row_smem(int w) { return (size_t)4 * w + (size_t)(5 * kRowThreads + 33) * sizeof(int); }
 
 cudaError_t blend_coeff_prepare(int max_smem_bytes) {
-    return cudaFuncSetAttribute(edt_rows_blend_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
+    cudaError_t e = cudaFuncSetAttribute(edt_row_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         max_smem_bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(edt_row_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem_bytes);
 }
 
 cudaError_t launch_blend_coeff(const unsigned char* label, int h, int w, long long pitch, float* blend,
                                int blend_pitch, void* scratch, cudaStream_t s) {
-    uint32_t* gq = static_cast<uint32_t*>(scratch);
-    edt_cols_kernel<<<(w + kColW - 1) / kColW, dim3(kColW, kColTY), 0, s>>>(label, h, w, pitch, gq);
+    uint16_t* g1 = static_cast<uint16_t*>(scratch);
+    uint16_t* g2 = g1 + (size_t)h * w;
+    float* dist1 = reinterpret_cast<float*>(g2 + (size_t)h * w);
+    edt_cols_kernel<<<(w + kColW - 1) / kColW, dim3(kColW, kColTY), 0, s>>>(label, h, w, pitch, g1, g2);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    edt_rows_blend_kernel<<<h, kRowThreads, blend_coeff_row_smem(w), s>>>(label, h, w, pitch, gq, blend,
-                                                                          blend_pitch);
+    const size_t smem = blend_coeff_row_smem(w);
+    edt_row_kernel<false><<<h, kRowThreads, smem, s>>>(label, h, w, pitch, g1, dist1, blend, blend_pitch);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    edt_row_kernel<true><<<h, kRowThreads, smem, s>>>(label, h, w, pitch, g2, dist1, blend, blend_pitch);
     return cudaGetLastError();
 }
 

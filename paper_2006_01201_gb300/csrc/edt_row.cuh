@@ -3,7 +3,7 @@
 // plain arrays (device functions under nvcc, plain inline functions under a
 // host compiler); the kernel in edt.cu orders them with barriers and scans.
 //
-// Row pass, per area a (0: Area1, 1: Area2) of one canvas row: the squared
+// Row pass, for one area (Area1 or Area2) and one canvas row: the squared
 // distance at column x is
 //   d2(x) = min over sites q of (x - q)^2 + f(q),   f(q) = g(q)^2,
 // g(q) the vertical distance of column q to its nearest feature pixel
@@ -44,12 +44,11 @@ namespace edt {
 
 constexpr uint32_t kNoSite = 0xFFFFu;  // g of a column without a feature pixel of the area
 
-// g of column q for area a from the packed row (g of Area1 in the low half,
-// of Area2 in the high half)
-PANO_HD uint32_t g_of(const uint32_t* gs, int w, int a, int q) { return (PANO_AT(gs, q, w, 520) >> (16 * a)) & 0xFFFFu; }
+// g of column q of the row of one area
+PANO_HD uint32_t g_of(const uint16_t* gs, int w, int q) { return PANO_AT(gs, q, w, 520); }
 
-PANO_HD long long f_of(const uint32_t* gs, int w, int a, int q) {
-    const long long v = g_of(gs, w, a, q);
+PANO_HD long long f_of(const uint16_t* gs, int w, int q) {
+    const long long v = g_of(gs, w, q);
     return v * v;
 }
 
@@ -76,19 +75,30 @@ PANO_HD bool owns(long long fp, int p, long long fq, int q, int x) {
 }
 
 // Step 1: envelope of the sites of columns [x0, x1), stored at st[x0 ..];
-// returns their count.
-PANO_HD int band_envelope(const uint32_t* gs, uint16_t* st, int w, int a, int x0, int x1) {
+// returns their count. The two top sites and their f stay in registers.
+PANO_HD int band_envelope(const uint16_t* gs, uint16_t* st, int w, int x0, int x1) {
     int k = 0;
+    int t1 = 0, t2 = 0;  // top and second site (valid for k >= 1, k >= 2)
+    long long f1 = 0, f2 = 0;
     for (int q = x0; q < x1; ++q) {
-        if (g_of(gs, w, a, q) == kNoSite) continue;
-        const long long fq = f_of(gs, w, a, q);
-        while (k >= 2) {
-            const int b = PANO_AT(st, x0 + k - 1, w, 521), p = PANO_AT(st, x0 + k - 2, w, 521);
-            if (hidden(f_of(gs, w, a, p), p, f_of(gs, w, a, b), b, fq, q)) --k;
-            else break;
+        const uint32_t gq = g_of(gs, w, q);
+        if (gq == kNoSite) continue;
+        const long long fq = (long long)gq * gq;
+        while (k >= 2 && hidden(f2, t2, f1, t1, fq, q)) {
+            --k;  // pop t1
+            t1 = t2;
+            f1 = f2;
+            if (k >= 2) {
+                t2 = PANO_AT(st, x0 + k - 2, w, 521);
+                f2 = f_of(gs, w, t2);
+            }
         }
         PANO_AT(st, x0 + k, w, 522) = (uint16_t)q;
         ++k;
+        t2 = t1;
+        f2 = f1;
+        t1 = q;
+        f1 = fq;
     }
     return k;
 }
@@ -112,58 +122,65 @@ PANO_HD int next_kept(const int* lo, const int* hi, int nb, int b, int last) {
 // Band b keeps st[lo[b] .. hi[b]); the merge lowers hi[] at the end of the
 // left group and raises lo[] at the start of the right one. The left group
 // keeps at least its first site and the right one its last, so the merged
-// group runs from lf to rl. Returns false if the iteration limit (more steps
-// than there are sites, which a valid input never needs) was reached.
-PANO_HD bool merge_groups(const uint32_t* gs, const uint16_t* st, int* lo, int* hi, int w, int nb, int a, int lf,
+// group runs from lf to rl. The top of the merged stack (the left's last
+// site l1 and the right site q being pushed) stays in registers. Returns
+// false if the iteration limit (more steps than there are sites, which a
+// valid input never needs) was reached.
+PANO_HD bool merge_groups(const uint16_t* gs, const uint16_t* st, int* lo, int* hi, int w, int nb, int lf,
                           int ll, int rf, int rl) {
-    int lb = ll;               // band of the left group's last kept site
-    int sb = rf, si = PANO_AT(lo, rf, nb, 525);  // first right site still kept: st[si] of band sb
-    bool pushed = false;       // st[si] is on the merged stack
+    int lb = ll;  // band of the left's last kept site l1 = st[lhi - 1]
+    int llo = PANO_AT(lo, lb, nb, 525), lhi = PANO_AT(hi, lb, nb, 525);
+    int l1 = PANO_AT(st, lhi - 1, w, 526);
+    long long f1 = f_of(gs, w, l1);
+    int sb = rf, si = PANO_AT(lo, rf, nb, 527);  // q = st[si] of band sb: the right site being pushed
+    int q = PANO_AT(st, si, w, 528);
+    long long fq = f_of(gs, w, q);
     bool ok = false;
     for (int it = 0; it <= 2 * w + 2; ++it) {
-        if (!pushed) {
-            // push st[si]: first pop the left sites it hides (the left keeps >= 1)
-            const int q = PANO_AT(st, si, w, 526);
-            const long long fq = f_of(gs, w, a, q);
-            for (int pops = 0; pops <= w; ++pops) {
-                const int n = PANO_AT(hi, lb, nb, 527) - PANO_AT(lo, lb, nb, 527);
-                int l2;
-                if (n >= 2) {
-                    l2 = PANO_AT(st, hi[lb] - 2, w, 528);
-                } else {
-                    const int pb = prev_kept(lo, hi, nb, lb, lf);
-                    if (pb < 0) break;
-                    l2 = PANO_AT(st, hi[pb] - 1, w, 528);
-                }
-                const int l1 = PANO_AT(st, hi[lb] - 1, w, 529);
-                if (!hidden(f_of(gs, w, a, l2), l2, f_of(gs, w, a, l1), l1, fq, q)) break;
-                if (--hi[lb] == lo[lb]) lb = prev_kept(lo, hi, nb, lb, lf);
+        // push q: first pop the left sites it hides (the left keeps >= 1)
+        for (int pops = 0; pops <= w; ++pops) {
+            int pb = lb, i2 = lhi - 2;  // l2 = st[i2] of band pb, the site below l1
+            if (i2 < llo) {
+                pb = prev_kept(lo, hi, nb, lb, lf);
+                if (pb < 0) break;
+                i2 = PANO_AT(hi, pb, nb, 529) - 1;
             }
-            pushed = true;
-            continue;
+            const int l2 = PANO_AT(st, i2, w, 530);
+            const long long f2 = f_of(gs, w, l2);
+            if (!hidden(f2, l2, f1, l1, fq, q)) break;
+            if (--lhi == llo) {  // band lb loses its last kept site
+                PANO_AT(hi, lb, nb, 531) = lhi;
+                lb = pb;
+                llo = PANO_AT(lo, lb, nb, 531);
+                lhi = PANO_AT(hi, lb, nb, 531);
+            }
+            l1 = l2;
+            f1 = f2;
         }
-        // st[si] is pushed: look at the right site after it
+        // q is pushed: the right site after it
         int nbd = sb, ni = si + 1;
-        if (ni >= PANO_AT(hi, sb, nb, 530)) {
+        if (ni >= PANO_AT(hi, sb, nb, 532)) {
             nbd = next_kept(lo, hi, nb, sb, rl);
             if (nbd < 0) {
                 ok = true;  // every right site processed
                 break;
             }
-            ni = lo[nbd];
+            ni = PANO_AT(lo, nbd, nb, 533);
         }
-        const int top = PANO_AT(st, si, w, 531), q = PANO_AT(st, ni, w, 531), l1 = PANO_AT(st, hi[lb] - 1, w, 531);
-        if (hidden(f_of(gs, w, a, l1), l1, f_of(gs, w, a, top), top, f_of(gs, w, a, q), q)) {
-            sb = nbd;  // st[si] is popped; the next right site comes next
-            si = ni;
-            pushed = false;
-        } else {
-            ok = true;  // q lands on a right site: the rest of the right envelope stays
+        const int q2 = PANO_AT(st, ni, w, 534);
+        const long long fq2 = f_of(gs, w, q2);
+        if (!hidden(f1, l1, fq, q, fq2, q2)) {
+            ok = true;  // q2 lands on q: the rest of the right envelope stays
             break;
         }
+        sb = nbd;  // q is popped; q2 is pushed next
+        si = ni;
+        q = q2;
+        fq = fq2;
     }
-    for (int b = rf; b < sb; ++b) PANO_AT(lo, b, nb, 532) = hi[b];  // popped right bands
-    PANO_AT(lo, sb, nb, 533) = si;
+    PANO_AT(hi, lb, nb, 535) = lhi;
+    for (int b = rf; b < sb; ++b) PANO_AT(lo, b, nb, 536) = hi[b];  // popped right bands
+    PANO_AT(lo, sb, nb, 537) = si;
     return ok;
 }
 
@@ -184,48 +201,60 @@ PANO_HD int region_start(long long fp, int p, long long fq, int q, int w) {
 // no site holds the start of the next band with one (w if none), so zs is
 // non-decreasing. nxt[b]: the first band >= b that keeps a site (nb if none).
 struct Walker {
-    int b, j;  // the owner is st[j] of band b
+    int b, j, hb;  // the owner is st[j] of band b; hb = hi[b]
+    int s;         // the owner's column
+    long long fs;  // and its f
 };
 
-PANO_HD Walker walk_start(const uint32_t* gs, const uint16_t* st, const int* lo, const int* hi, const int* zs, int w,
-                          int nb, int a, int x) {
+PANO_HD Walker walk_start(const uint16_t* gs, const uint16_t* st, const int* lo, const int* hi, const int* zs, int w,
+                          int nb, int x) {
     int l = 0, r = nb - 1;  // largest b with zs[b] <= x (zs[first kept band] = -1)
     while (l < r) {
         const int m = (l + r + 1) >> 1;
-        if (PANO_AT(zs, m, nb, 534) <= x) l = m;
+        if (PANO_AT(zs, m, nb, 538) <= x) l = m;
         else r = m - 1;
     }
     Walker k;
     k.b = l;
-    k.j = PANO_AT(lo, l, nb, 535);
-    for (int it = 0; it < w && k.j + 1 < PANO_AT(hi, l, nb, 535); ++it) {
-        const int p = PANO_AT(st, k.j, w, 536), q = PANO_AT(st, k.j + 1, w, 536);
-        if (!owns(f_of(gs, w, a, p), p, f_of(gs, w, a, q), q, x)) break;
+    k.j = PANO_AT(lo, l, nb, 539);
+    k.hb = PANO_AT(hi, l, nb, 539);
+    k.s = PANO_AT(st, k.j, w, 540);
+    k.fs = f_of(gs, w, k.s);
+    for (int it = 0; it < w && k.j + 1 < k.hb; ++it) {
+        const int q = PANO_AT(st, k.j + 1, w, 541);
+        const long long fq = f_of(gs, w, q);
+        if (!owns(k.fs, k.s, fq, q, x)) break;
         ++k.j;
+        k.s = q;
+        k.fs = fq;
     }
     return k;
 }
 
 // moves the walker to the owner of column x (x not left of the last one)
 // and returns d2(x)
-PANO_HD long long walk_to(const uint32_t* gs, const uint16_t* st, const int* lo, const int* hi, const int* nxt, int w,
-                          int nb, int a, int x, Walker* k) {
+PANO_HD long long walk_to(const uint16_t* gs, const uint16_t* st, const int* lo, const int* hi, const int* nxt, int w,
+                          int nb, int x, Walker* k) {
     for (int it = 0; it < w; ++it) {
-        int b = k->b, j = k->j + 1;
-        if (j >= PANO_AT(hi, b, nb, 537)) {
+        int b = k->b, j = k->j + 1, hb = k->hb;
+        if (j >= hb) {
             if (b + 1 >= nb) break;
-            b = PANO_AT(nxt, b + 1, nb, 538);
+            b = PANO_AT(nxt, b + 1, nb, 542);
             if (b >= nb) break;
-            j = lo[b];
+            j = PANO_AT(lo, b, nb, 543);
+            hb = PANO_AT(hi, b, nb, 543);
         }
-        const int p = PANO_AT(st, k->j, w, 539), q = PANO_AT(st, j, w, 539);
-        if (!owns(f_of(gs, w, a, p), p, f_of(gs, w, a, q), q, x)) break;
+        const int q = PANO_AT(st, j, w, 544);
+        const long long fq = f_of(gs, w, q);
+        if (!owns(k->fs, k->s, fq, q, x)) break;
         k->b = b;
         k->j = j;
+        k->hb = hb;
+        k->s = q;
+        k->fs = fq;
     }
-    const int s = PANO_AT(st, k->j, w, 540);
-    const long long dx = x - s;
-    return dx * dx + f_of(gs, w, a, s);
+    const long long dx = x - k->s;
+    return dx * dx + k->fs;
 }
 
 }  // namespace edt

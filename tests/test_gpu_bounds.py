@@ -168,7 +168,7 @@ def test_blends_and_warp_keep_every_index_in_bounds(libs, monkeypatch, h, w, c):
 
 @pytest.mark.parametrize("h,w,kind", [(37, 61, "blobs"), (1, 200, "blobs"), (150, 1, "blobs"), (40, 90, "no_area1"),
                                       (33, 47, "area3_only"), (64, 300, "single_sites"), (2100, 7, "single_sites"),
-                                      (3, 9000, "blobs"), (5, 20000, "single_sites")])
+                                      (3, 9000, "blobs"), (5, 40000, "single_sites")])
 def test_distance_transform_keeps_every_index_in_bounds(libs, monkeypatch, h, w, kind):
     g = np.random.default_rng(9)
     if kind == "blobs":

@@ -129,11 +129,11 @@ def _sampled(label, n, seed):
 
 
 def test_wide_canvas_many_columns_per_band():
-    """26000 columns (51 per thread of the row pass, near the shared-memory
+    """56000 columns (219 per thread of the row pass, near the shared-memory
     limit), wavy seams, holes and scattered Area1/Area2 pixels."""
-    label = overlap_canvas(24, 26000, 10)
+    label = overlap_canvas(12, 56000, 10)
     g = np.random.default_rng(11)
-    label[g.integers(0, 24, 300), g.integers(0, 26000, 300)] = g.choice([1, 2], 300)
+    label[g.integers(0, 12, 300), g.integers(0, 56000, 300)] = g.choice([1, 2], 300)
     _sampled(label, 400, 12)
 
 
@@ -160,7 +160,7 @@ def test_dense_random_labels_sampled(shape, seed):
 
 
 def test_too_wide_canvas_is_refused():
-    lab = torch.full((2, 27000), 3, dtype=torch.uint8, device=DEV)
+    lab = torch.full((2, 60000), 3, dtype=torch.uint8, device=DEV)
     with pytest.raises(binding.PanoError) as e:
         binding.blend_coeff(lab)
     assert e.value.status == binding.PANO_ERR_UNSUPPORTED
