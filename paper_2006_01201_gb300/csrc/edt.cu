@@ -54,10 +54,14 @@ __device__ __forceinline__ void col_masks(const unsigned char* __restrict__ labe
                                           int h, int x, int y0, uint32_t* m1, uint32_t* m2) {
     uint32_t a = 0, b = 0;
     const int n = min(32, h - y0);
-    for (int i = 0; i < n; ++i) {
-        const unsigned char c = __ldg(&PANO_AT(label, (long long)(y0 + i) * pitch + x, nl, 501));
-        a |= (uint32_t)(c == 1) << i;
-        b |= (uint32_t)(c == 2) << i;
+    const unsigned char* p = label + (long long)y0 * pitch + x;
+#pragma unroll 8
+    for (int i = 0; i < 32; ++i) {
+        if (i < n) {
+            const unsigned char c = __ldg(&PANO_AT(p, (long long)i * pitch, nl - ((long long)y0 * pitch + x), 501));
+            a |= (uint32_t)(c == 1) << i;
+            b |= (uint32_t)(c == 2) << i;
+        }
     }
     *m1 = a;
     *m2 = b;
@@ -122,7 +126,9 @@ __global__ void __launch_bounds__(kColW * kColTY, 2) edt_cols_kernel(const unsig
         }
         if (col_in && y0 < h) {
             const int n = min(32, h - y0);
-            for (int i = 0; i < n; ++i) {
+#pragma unroll 8
+            for (int i = 0; i < 32; ++i) {
+                if (i >= n) break;
                 const int yy = y0 + i;
                 uint32_t g[2];
 #pragma unroll
@@ -239,6 +245,29 @@ __global__ void __launch_bounds__(kRowThreads, kRowCtas) edt_row_kernel(const un
     for (int i = tid; i < w; i += NB) PANO_AT(gs, i, w, 505) = PANO_AT(gplane, (long long)y * w + i, ng, 506);
     __syncthreads();
     const int x0 = min(w, tid * bw), x1 = min(w, x0 + bw);
+    {
+        // step 0: the runs of equal g at the band's edges, against the
+        // columns before and after them (found by scans over the bands)
+        int ls, fe;
+        band_run_edges(gs, w, x0, x1, &ls, &fe);
+        const int ps = block_prefix_max(ls, s_warp);
+        const int sf = block_suffix_min(fe, s_warp);
+        zs[tid] = ps;
+        glast[tid] = sf;
+        __syncthreads();
+        int L = -1, R = w;
+        if (x0 < x1) {
+            const int u = (x0 == 0 || gs[x0] != gs[x0 - 1]) ? x0 : (tid > 0 ? zs[tid - 1] : 0);
+            const int v = (x1 == w || gs[x1 - 1] != gs[x1]) ? x1 - 1 : (tid + 1 < NB ? glast[tid + 1] : w - 1);
+            L = u - 1;
+            R = v + 1;
+        }
+        edge_runs_hidden(gs, st, w, x0, x1, L, R);
+        __syncthreads();
+        for (int q = x0; q < x1; ++q)
+            if (st[q]) gs[q] = (uint16_t)kNoSite;
+        __syncthreads();
+    }
     {
         const int k = band_envelope(gs, st, w, x0, x1);
         PANO_AT(lo, tid, NB, 507) = x0;

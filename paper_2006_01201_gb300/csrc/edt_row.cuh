@@ -74,6 +74,52 @@ PANO_HD bool owns(long long fp, int p, long long fq, int q, int x) {
     return n <= (long long)x * d;
 }
 
+// Step 0 (optional, changes no d2): sites that two other sites hide have
+// no part of the envelope of the whole row, so they can be dropped before
+// it is built. Here g is often a staircase of plateaus (equal g over many
+// columns), and the first columns of a higher plateau are hidden by the
+// last column of the lower plateau before it and their right neighbour.
+// Inside a band the band envelope drops them; at a band's edges the merges
+// would pop them one by one. So each thread tests the run of equal g that
+// its band starts with against the column L before that run (if its g is
+// smaller), and the run it ends with against the column R after that run.
+// Marks the dropped columns of [x0, x1) with 1 in flag[] (0 elsewhere).
+PANO_HD void edge_runs_hidden(const uint16_t* gs, uint16_t* flag, int w, int x0, int x1, int L, int R) {
+    for (int q = x0; q < x1; ++q) PANO_AT(flag, q, w, 545) = 0;
+    if (x0 >= x1) return;
+    const uint32_t G = g_of(gs, w, x0);
+    if (G != kNoSite && G != 0 && L >= 0 && g_of(gs, w, L) < G) {  // kNoSite is no smaller
+        const long long fL = f_of(gs, w, L), fG = (long long)G * G;
+        for (int q = x0; q < x1 && g_of(gs, w, q) == G; ++q) {
+            const int c = q + 1;
+            if (c >= w || g_of(gs, w, c) == kNoSite) break;
+            if (hidden(fL, L, fG, q, f_of(gs, w, c), c)) flag[q] = 1;
+        }
+    }
+    const uint32_t H = g_of(gs, w, x1 - 1);
+    if (H != kNoSite && H != 0 && R < w && g_of(gs, w, R) < H) {
+        const long long fR = f_of(gs, w, R), fH = (long long)H * H;
+        for (int q = x1 - 1; q >= x0 && g_of(gs, w, q) == H; --q) {
+            const int c = q - 1;
+            if (c < 0 || g_of(gs, w, c) == kNoSite) break;
+            if (hidden(f_of(gs, w, c), c, fH, q, fR, R)) flag[q] = 1;
+        }
+    }
+}
+
+// where runs of equal g begin and end in [x0, x1): the last column c with
+// c == 0 or g[c] != g[c-1] (-1 if none) and the first column c with
+// c == w-1 or g[c] != g[c+1] (w if none)
+PANO_HD void band_run_edges(const uint16_t* gs, int w, int x0, int x1, int* last_start, int* first_end) {
+    int ls = -1, fe = w;
+    for (int c = x0; c < x1; ++c) {
+        if (c == 0 || g_of(gs, w, c) != g_of(gs, w, c - 1)) ls = c;
+        if (fe == w && (c == w - 1 || g_of(gs, w, c) != g_of(gs, w, c + 1))) fe = c;
+    }
+    *last_start = ls;
+    *first_end = fe;
+}
+
 // Step 1: envelope of the sites of columns [x0, x1), stored at st[x0 ..];
 // returns their count. The two top sites and their f stay in registers.
 PANO_HD int band_envelope(const uint16_t* gs, uint16_t* st, int w, int x0, int x1) {
@@ -132,6 +178,11 @@ PANO_HD bool merge_groups(const uint16_t* gs, const uint16_t* st, int* lo, int* 
     int llo = PANO_AT(lo, lb, nb, 525), lhi = PANO_AT(hi, lb, nb, 525);
     int l1 = PANO_AT(st, lhi - 1, w, 526);
     long long f1 = f_of(gs, w, l1);
+    // the site below l1 (l2 = st[i2] of band pb; pb < 0: l1 is the left's only site), found once
+    // and again only after a pop
+    int pb = -1, l2 = 0;
+    long long f2 = 0;
+    bool have2 = false;
     int sb = rf, si = PANO_AT(lo, rf, nb, 527);  // q = st[si] of band sb: the right site being pushed
     int q = PANO_AT(st, si, w, 528);
     long long fq = f_of(gs, w, q);
@@ -139,15 +190,20 @@ PANO_HD bool merge_groups(const uint16_t* gs, const uint16_t* st, int* lo, int* 
     for (int it = 0; it <= 2 * w + 2; ++it) {
         // push q: first pop the left sites it hides (the left keeps >= 1)
         for (int pops = 0; pops <= w; ++pops) {
-            int pb = lb, i2 = lhi - 2;  // l2 = st[i2] of band pb, the site below l1
-            if (i2 < llo) {
-                pb = prev_kept(lo, hi, nb, lb, lf);
-                if (pb < 0) break;
-                i2 = PANO_AT(hi, pb, nb, 529) - 1;
+            if (!have2) {
+                int i2 = lhi - 2;
+                pb = lb;
+                if (i2 < llo) {
+                    pb = prev_kept(lo, hi, nb, lb, lf);
+                    if (pb >= 0) i2 = PANO_AT(hi, pb, nb, 529) - 1;
+                }
+                if (pb >= 0) {
+                    l2 = PANO_AT(st, i2, w, 530);
+                    f2 = f_of(gs, w, l2);
+                }
+                have2 = true;
             }
-            const int l2 = PANO_AT(st, i2, w, 530);
-            const long long f2 = f_of(gs, w, l2);
-            if (!hidden(f2, l2, f1, l1, fq, q)) break;
+            if (pb < 0 || !hidden(f2, l2, f1, l1, fq, q)) break;
             if (--lhi == llo) {  // band lb loses its last kept site
                 PANO_AT(hi, lb, nb, 531) = lhi;
                 lb = pb;
@@ -156,6 +212,7 @@ PANO_HD bool merge_groups(const uint16_t* gs, const uint16_t* st, int* lo, int* 
             }
             l1 = l2;
             f1 = f2;
+            have2 = false;
         }
         // q is pushed: the right site after it
         int nbd = sb, ni = si + 1;
