@@ -133,12 +133,14 @@ __global__ void __launch_bounds__(kColW * kColTY, 2) edt_cols_kernel(const unsig
                 uint32_t g[2];
 #pragma unroll
                 for (int a = 0; a < 2; ++a) {
-                    const uint32_t up = m[a] & (0xFFFFFFFFu >> (31 - i));  // rows y0 .. yy
-                    const uint32_t dn = m[a] & (0xFFFFFFFFu << i);         // rows yy .. y0 + 31
-                    const int ab = up ? y0 + 31 - __clz(up) : above[a];
-                    const int be = dn ? y0 + __ffs(dn) - 1 : below[a];
-                    const long long d = min((long long)yy - ab, (long long)be - yy);
-                    g[a] = d >= (long long)edt::kNoSite ? edt::kNoSite : (uint32_t)d;
+                    const uint32_t up = m[a] << (31 - i);  // rows y0 .. yy, row yy in bit 31
+                    const uint32_t dn = m[a] >> i;         // rows yy .. y0 + 31, row yy in bit 0
+                    // distances above and below (ints: rows < 2^16, the no-feature
+                    // values keep both differences below 2^31)
+                    const int da = up ? __clz(up) : yy - above[a];
+                    const int db = dn ? __ffs(dn) - 1 : below[a] - yy;
+                    const int d = min(da, db);
+                    g[a] = d >= (int)edt::kNoSite ? edt::kNoSite : (uint32_t)d;
                 }
                 PANO_AT(g1, (long long)yy * w + x, ng, 504) = (uint16_t)g[0];
                 PANO_AT(g2, (long long)yy * w + x, ng, 504) = (uint16_t)g[1];
