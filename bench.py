@@ -616,12 +616,15 @@ def run_blend_coeff(args):
         binding.blend_coeff(label, out=out, scratch=scratch)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    sampler.start()
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record()
         binding.blend_coeff(label, out=out, scratch=scratch)
         ev[k][1].record()
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     ms = sum(a_.elapsed_time(b_) for a_, b_ in ev) / args.steps
     npx = h * w
     alg = 5 * npx          # label read (1 B) and Blend written (4 B) once per pixel
@@ -636,7 +639,8 @@ def run_blend_coeff(args):
             "roofline": {"bound": "hbm", "achieved": alg / (ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
                          "frac": alg / (ms * 1e-3) / 1e9 / peak, "traffic": None,
                          "kernel": "edt_cols_kernel + edt_row_kernel (Area1) + edt_row_kernel (Area2)", "alg_bytes_per_launch": alg,
-                         "peak_source": f"{src} hbm_gbs"}}
+                         "peak_source": f"{src} hbm_gbs"},
+            "gpu_launches": 3 * args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -664,12 +668,15 @@ def run_refine(args):
         binding.energy_grad(T, J, u, 0.05)
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sampler = ClockSampler(0)
+    sampler.start()
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record()
         binding.energy_grad(T, J, u, 0.05)
         ev[k][1].record()
     torch.cuda.synchronize()
+    clocks = sampler.stop()
     ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
     npx = 1024 * 1024
     # per pixel: T 4 B, J taps ~4 B, u 8 B (+ neighbours from cache), dE/du 8 B,
@@ -693,7 +700,8 @@ def run_refine(args):
                          "alg_bytes_per_launch": alg, "peak_source": f"{src} hbm_gbs"},
             "refinement": {"levels": 5, "adam_steps_per_level": 20, "seconds": t_ref,
                            "mean_epe_px_vs_truth": float(err.mean()),
-                           "energy_per_level": [[l, a, b] for l, a, b in trace]}}
+                           "energy_per_level": [[l, a, b] for l, a, b in trace]},
+            "gpu_launches": args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
@@ -978,7 +986,10 @@ def run_compose(args):
         torch.cuda.synchronize()
         return sum(a.elapsed_time(b) for a, b in ev) / args.steps
 
+    sampler = ClockSampler(0)
+    sampler.start()
     ms = timed(lambda: binding.compose_pair(Ld, Rd, labd, Bd, lr, rl, origin=(0, m), params=params, out=F))
+    clocks = sampler.stop()
 
     def stitch():
         ctx.flow_pair(Lc, Rc, out=(lr, rl))
@@ -1002,7 +1013,7 @@ def run_compose(args):
                          "peak_source": f"{src} hbm_gbs"},
             "stitch": {"metric": "overlap megapixels/sec (flow of the overlap + Code 1 on the canvas)",
                        "value": h * ws / (ms_stitch * 1e-3) / 1e6, "unit": "MP/s", "ms_per_step": ms_stitch},
-            "gpu_launches": 1}
+            "gpu_launches": args.steps, "clocks": clocks}
     print(json.dumps(line), flush=True)
     return 0
 
