@@ -41,19 +41,25 @@ SMALL_WORKLOAD = {"workload": "pair_256x512_gray_f32_lv4", "h": 256, "w": 512, "
 L2_FLUSH_BYTES = 256 << 20   # > 129 MB L2
 STREAM_MIN_PIXELS = 50000    # levels with at least this many pixels use the streamed LK kernel
 SMALL_TILE_PIXELS = 16000    # tiled levels below this many pixels use 16 x 8 tiles
-# DRAM bytes (read + write) per launch of the dominant kernel, averaged over
-# its launches in one step, from an ncu capture of the current kernel with
-# float32 pyramid planes (the 16-bit instantiations are other kernels: no
-# figure); None when the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = {"lk_stream_kernel": (1.188352e6 + 4.644352e6 + 18.470656e6 + 173.016832e6) / 4}
-# Warp instructions per launch of the dominant kernel from the same capture
-# (smsp__inst_executed.sum, averaged over its launches in one step).
-INST_PER_LAUNCH = {"lk_stream_kernel": (10558682 + 32560009 + 90773349 + 368200597) / 4}
+# ncu counters of the dominant kernels (DRAM bytes and warp instructions per
+# launch), written by `--ingest-ncu` from a capture into profiles/ together
+# with a digest of the sources the kernel is compiled from. A counter whose
+# digest no longer matches those sources belongs to an older kernel and is
+# reported as null.
+KERNEL_SOURCES = {
+    "lk_stream_kernel": ["paper_2006_01201_gb300/csrc/lk_stream_impl.cuh",
+                         "paper_2006_01201_gb300/csrc/lk_stream.cu",
+                         "paper_2006_01201_gb300/csrc/common.cuh"],
+    "blend_kernel": ["paper_2006_01201_gb300/csrc/blend.cu", "paper_2006_01201_gb300/csrc/common.cuh"],
+}
+KERNEL_SOURCES["lk_stream_batch_kernel"] = KERNEL_SOURCES["lk_stream_kernel"]
+KERNEL_SOURCES["rig_blend_kernel"] = KERNEL_SOURCES["blend_kernel"]
+COUNTER_FILES = {  # (kernel, workload) -> file under profiles/
+    ("lk_stream_kernel", "pair_4000x1500_rgb_u8_lv6"): "counters_lk_stream_kernel_pair_4000x1500_rgb_u8_lv6.json",
+    ("lk_stream_batch_kernel", "rig"): "counters_lk_stream_batch_kernel_rig_8x4000_rgb_u8_lv6.json",
+}
 # One warp instruction per scheduler per cycle, four schedulers per SM.
 SCHEDULERS_PER_SM = 4
-SMS = 152
-
-
 # ---------------------------------------------------------------------------
 # host-side helpers (no GPU needed; covered by the CPU tests)
 # ---------------------------------------------------------------------------
@@ -81,15 +87,115 @@ def lk_alg_bytes(h: int, w: int, levels: int, elem: int = 4):
     return out
 
 
-def path_alg_bytes(h: int, w: int, c: int, levels: int, in_bytes: int = 1, elem: int = 4):
-    """Algorithmic bytes of one step of the whole path (each array once);
-    elem = bytes of one stored pyramid element."""
+def path_alg_bytes(h: int, w: int, c: int, levels: int, in_bytes: int = 1, elem: int = 4,
+                   reduce_reread: bool = False):
+    """Algorithmic bytes of one step of the whole path, each persistent array
+    read once and written once (the K steps of a level fused on chip):
+      pyramid: read both strips (2 C in_bytes per pixel), write both luma
+               pyramids (2 elem per level pixel; a one-channel float strip
+               is its own level 0);
+      flow:    18 B per direction and level pixel with float32 levels (lk_alg_bytes);
+      blend:   read L and R (2 C in_bytes), both flows (16 B), write F (C in_bytes).
+    reduce_reread=True also counts each REDUCE re-reading its source level
+    (2 elem per pixel of every level but the last)."""
     npx = level_pixels(h, w, levels)
     n = h * w
-    pyramid = 2 * c * in_bytes * n + 2 * elem * sum(npx) + 2 * elem * sum(npx[:-1])  # read strips, write levels, re-read for REDUCE
+    own_l0 = c == 1 and in_bytes == 4 and elem == 4
+    pyramid = 2 * c * in_bytes * n + 2 * elem * (sum(npx) - (npx[0] if own_l0 else 0))
+    if reduce_reread:
+        pyramid += 2 * elem * sum(npx[:-1])
     flow = sum(lk_alg_bytes(h, w, levels, elem))
     blend = 2 * c * in_bytes * n + 16 * n + c * in_bytes * n
     return pyramid + flow + blend
+
+
+def source_digest(files) -> str:
+    """SHA-256 over the named repository files (path and contents)."""
+    import hashlib
+    d = hashlib.sha256()
+    for f in files:
+        d.update(f.encode())
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            d.update(fh.read())
+    return d.hexdigest()
+
+
+def read_counters(kernel: str, workload: str, profiles_dir: str = None):
+    """ncu counters of `kernel` on `workload` from profiles/, or None when
+    there are none or they were taken from other sources than the current ones."""
+    name = COUNTER_FILES.get((kernel, workload))
+    if not name:
+        return None
+    try:
+        with open(os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), name)) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if d.get("kernel") != kernel or d.get("sha256") != source_digest(KERNEL_SOURCES[kernel]):
+        return None
+    return d
+
+
+def _unit_scale(unit: str) -> float:
+    unit = unit.strip()
+    for prefix, f in (("K", 1e3), ("M", 1e6), ("G", 1e9), ("T", 1e12)):
+        if len(unit) > 1 and unit.startswith(prefix) and unit[1:] in ("byte", "inst", "cycle", "warp"):
+            return f
+    return 1.0
+
+
+def parse_ncu_raw_csv(path: str, kernel: str):
+    """Per-launch DRAM bytes, warp instructions and durations of the launches
+    of `kernel` (name prefix) in an `ncu -i REPORT --page raw --csv` export."""
+    import csv
+    with open(path, newline="") as f:
+        rows = list(csv.reader(f))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    head, units = rows[hi], rows[hi + 1]
+    col = {n: i for i, n in enumerate(head)}
+
+    def val(r, name):
+        i = col.get(name)
+        if i is None or i >= len(r) or not r[i].strip():
+            return None
+        return float(r[i].replace(",", "")) * _unit_scale(units[i])
+
+    out = []
+    for r in rows[hi + 2:]:
+        if len(r) <= col["Kernel Name"] or not r[col["Kernel Name"]].startswith(kernel):
+            continue
+        rd, wr = val(r, "dram__bytes_read.sum"), val(r, "dram__bytes_write.sum")
+        out.append({"name": r[col["Kernel Name"]],
+                    "dram_bytes": rd + wr if rd is not None and wr is not None else None,
+                    "warp_inst": val(r, "smsp__inst_executed.sum"),
+                    "duration_ns": val(r, "gpu__time_duration.sum")})
+    return out
+
+
+def ingest_ncu(csv_path: str, kernel: str, workload: str, command: str, profiles_dir: str = None) -> str:
+    """Write profiles/<counters file> for (kernel, workload) from an ncu raw
+    CSV export, stamped with the digest of the kernel's current sources."""
+    launches = parse_ncu_raw_csv(csv_path, kernel)
+    if not launches:
+        raise SystemExit(f"no launch of {kernel} in {csv_path}")
+
+    def mean(key):
+        v = [x[key] for x in launches if x[key] is not None]
+        return sum(v) / len(v) if v else None
+
+    d = {"kernel": kernel, "workload": workload, "sources": KERNEL_SOURCES[kernel],
+         "sha256": source_digest(KERNEL_SOURCES[kernel]), "command": command, "launches": launches,
+         "dram_bytes_per_launch": mean("dram_bytes"), "warp_inst_per_launch": mean("warp_inst")}
+    path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), COUNTER_FILES[(kernel, workload)])
+    with open(path, "w") as f:
+        json.dump(d, f, indent=1)
+        f.write("\n")
+    return path
+
+
+def sm_count(dev) -> int:
+    import torch
+    return int(torch.cuda.get_device_properties(dev).multi_processor_count)
 
 
 RIG_WORKLOAD = {"workload": "rig_8x4000x{800..2000}_rgb_u8_lv6_canvas_9000x4000", "h": 4000,
@@ -299,17 +405,19 @@ PAPER_CONTEXT = "under 30 s per 9000x4000 panorama for the whole workflow on an 
 LK_FLOPS_PER_PIXEL_STEP = 50
 
 
-def issue_roofline(kernel: str, launch_ms: float, sm_mhz):
-    """Warp-instruction issue rate of `kernel` (ncu instruction count per
+def issue_roofline(counters, launch_ms: float, sm_mhz, sms: int):
+    """Warp-instruction issue rate of a kernel (ncu instruction count per
     launch / live launch time) against the SMs' issue peak at the sampled SM
-    clock; None without a counted instruction total or a clock sample."""
-    inst = INST_PER_LAUNCH.get(kernel)
+    clock; None without current counters or a clock sample."""
+    inst = counters.get("warp_inst_per_launch") if counters else None
     if not inst or not launch_ms or not sm_mhz:
         return None
     achieved = inst / (launch_ms * 1e-3) / 1e9
-    peak = SMS * SCHEDULERS_PER_SM * sm_mhz * 1e6 / 1e9
+    peak = sms * SCHEDULERS_PER_SM * sm_mhz * 1e6 / 1e9
     return {"achieved": achieved, "peak": peak, "unit": "G warp-instr/s", "frac": achieved / peak,
-            "inst_per_launch": inst, "kernel": kernel, "peak_source": "152 SMs x 4 schedulers x sampled SM clock"}
+            "inst_per_launch": inst, "kernel": counters["kernel"],
+            "peak_source": f"{sms} SMs x 4 schedulers x sampled SM clock",
+            "counters": "profiles/" + COUNTER_FILES[(counters["kernel"], counters["workload"])]}
 
 
 def fp32_peak_tflops(sm_mhz: float = 2070.0, sms: int = 152) -> float:
@@ -375,13 +483,18 @@ def run_gpu(args):
     import torch
 
     rank, world, local = dist_env()
+    import synth
+    # the rig and the 16-bit forms ride along with the default single-GPU line
+    extras = world == 1 and args.workload == "pair" and args.pyr_dtype == "f32" and not args.no_rig
+    W = RIG_WORKLOAD
+    rig_pairs = synth.rig_pairs(h=W["h"], widths=W["widths"], dmax=W["dmax"], levels=W["levels"],
+                                workers=min(8, os.cpu_count() or 1)) if extras else None
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", init_method="env://")
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    import synth
     import paper_2006_01201_gb300 as pkg
     from paper_2006_01201_gb300 import build as gpu_build
 
@@ -472,14 +585,18 @@ def run_gpu(args):
     peak, peak_src = read_peaks()
     launch_ms = dk["ms"] / dk["launches"]
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9 if bytes_per_launch else None
+    # counters of the float32 kernel on this workload (16-bit planes run other kernels)
+    counters = read_counters(dominant, WL["workload"]) if args.pyr_dtype == "f32" else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None,
-                "traffic": TRAFFIC_PER_LAUNCH.get(dominant) if args.pyr_dtype == "f32" else None, "kernel": dominant,
+                "traffic": counters["dram_bytes_per_launch"] if counters else None, "kernel": dominant,
                 "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
-                "launches_per_step": launches_per_step, "peak_source": f"{peak_src} hbm_gbs"}
-    issue = issue_roofline(dominant, launch_ms, clocks["sm_mhz"] if clocks else None) \
-        if args.pyr_dtype == "f32" else None
-    path_bytes = path_alg_bytes(h, w, c, levels, elem=elem)
+                "launches_per_step": launches_per_step, "peak_source": f"{peak_src} hbm_gbs",
+                "counters": "profiles/" + COUNTER_FILES[(dominant, WL["workload"])] if counters else None}
+    issue = issue_roofline(counters, launch_ms, clocks["sm_mhz"] if clocks else None, sm_count(dev))
+    in_bytes = pair.L.dtype.itemsize
+    path_bytes = path_alg_bytes(h, w, c, levels, in_bytes=in_bytes, elem=elem)
+    path_bytes_rr = path_alg_bytes(h, w, c, levels, in_bytes=in_bytes, elem=elem, reduce_reread=True)
     path_gbs = path_bytes / (total_ms / args.steps * 1e-3) / 1e9
     stage_bytes = unfused_stage_bytes(h, w, levels, WL["iters"], elem)
     path_flops = 2 * WL["iters"] * LK_FLOPS_PER_PIXEL_STEP * sum(level_pixels(h, w, levels))
@@ -509,7 +626,11 @@ def run_gpu(args):
                 "config": dict(WL, l2="flushed between steps (256 MB write, untimed)",
                                parallelism=f"replicas{world}", pyr_dtype=args.pyr_dtype),
                 "roofline": roofline, "issue_roofline": issue,
-                "path": {"alg_bytes_per_step": path_bytes, "achieved_gbs": path_gbs, "frac": path_gbs / peak,
+                "path": {"alg_bytes_per_step": path_bytes, "alg_bytes_per_px": path_bytes / (h * w),
+                         "achieved_gbs": path_gbs, "frac": path_gbs / peak,
+                         "model": "each persistent array read once, written once; K steps of a level fused",
+                         "with_reduce_reread": {"alg_bytes_per_step": path_bytes_rr,
+                                                "frac": path_bytes_rr / (total_ms / args.steps * 1e-3) / 1e9 / peak},
                          "unfused_stage_bytes_per_step": stage_bytes,
                          "fp32_tflops": path_flops / (total_ms / args.steps * 1e-3) / 1e12,
                          "fp32_peak_tflops": fp32_peak_tflops(clocks["sm_mhz"] if clocks else 2070.0),
@@ -542,8 +663,22 @@ def run_gpu(args):
             if pyr_fmt:
                 line["half_precision"] = half_precision_report(pkg, pair, levels, pyr_fmt, g_lr, g_rl,
                                                                F.cpu().numpy(), olr, orl, dev)
+            if extras:
+                line["half"] = {"pair": pair_half_report(pkg, dev, pair, levels, args.steps, args.warmup, value,
+                                                         g_lr, g_rl, F.cpu().numpy(), olr, orl)}
             line["cpu_baseline"] = oracle_baseline(pair, levels, args.cpu_budget, f"of the {h}x{w} pair")
             line["cpu_baseline"]["full_pair_flow_s"] = t_full
+        if extras:
+            oflows = None
+            if not args.no_cpu_baseline:
+                t0 = time.perf_counter()
+                oflows = rig_oracle_flows(rig_pairs, W["levels"])
+                t_rig_oracle = time.perf_counter() - t0
+            rr = rig_report(dev, rig_pairs, args.steps, args.warmup, oracle_flows=oflows)
+            if oflows is not None:
+                rr["oracle_flow_s"] = t_rig_oracle
+            line.setdefault("half", {})["rig"] = rr.pop("half", None)
+            line["rig"] = rr
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -582,6 +717,62 @@ def half_precision_report(pkg, pair, levels, pyr_fmt, g_lr, g_rl, g_F, olr, orl,
                                 "frac_gt_1lsb": float((d32 > 1).mean())},
             "F_u8_vs_exact_oracle": {"max_lsb": int(do.max()), "mean_lsb": float(do.mean()),
                                      "frac_gt_1lsb": float((do > 1).mean())}}
+
+
+def pair_half_report(pkg, dev, pair, levels, steps, warmup, value32, g_lr, g_rl, g_F, olr, orl):
+    """The pair in bfloat16 and binary16 pyramid storage: throughput (same
+    loop as the float32 line), flows against the exact FP64 oracle, the
+    storage-matched oracle and the float32 GPU path, and F against the float32
+    GPU path and the oracle's whole path."""
+    import numpy as np
+    import torch
+    import oracle
+
+    h, w = pair.L.shape[:2]
+    c = pair.L.shape[2] if pair.L.ndim == 3 else 1
+    L = torch.from_numpy(pair.L).to(dev)
+    R = torch.from_numpy(pair.R).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    Fo = oracle.quantize_u8(oracle.blend(pair.L, pair.R, olr, orl, oracle.Params(levels=levels)))
+    out = {"fp32_value": value32, "bound": "mean EPE <= 0.05 px per direction against the exact FP64 oracle"}
+    for dt in ("bf16", "f16"):
+        code, fmt, _ = PYR_DTYPES[dt]
+        with pkg.FlowContext(pkg.Params(levels=levels, pyr_dtype=code), max_h=h, max_w=w, max_c=c) as ctx:
+            lr = torch.empty((h, w, 2), dtype=torch.float32, device=dev)
+            rl = torch.empty((h, w, 2), dtype=torch.float32, device=dev)
+            F = torch.empty_like(L)
+
+            def step():
+                ctx.flow_pair(L, R, out=(lr, rl), stream=stream)
+                ctx.blend_pair(L, R, lr, rl, out=F, stream=stream)
+
+            for _ in range(warmup):
+                flush.zero_()
+                step()
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+            for k in range(steps):
+                flush.zero_()
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+            torch.cuda.synchronize()
+            ms = sum(a_.elapsed_time(b_) for a_, b_ in ev)
+            hlr, hrl, hF = lr.cpu().numpy(), rl.cpu().numpy(), F.cpu().numpy()
+        slr, srl = oracle.flow_pair(pair.L, pair.R, oracle.Params(levels=levels, pyr_fmt=fmt))
+        d32 = np.abs(hF.astype(int) - g_F.astype(int))
+        do = np.abs(hF.astype(int) - Fo.astype(int))
+        ex = [mean_epe(hlr, olr), mean_epe(hrl, orl)]
+        out[dt] = {"value": throughput(h * w, steps, 1, ms), "unit": UNIT, "ms_per_step": ms / steps,
+                   "epe_vs_exact_oracle": ex, "epe_vs_storage_oracle": [mean_epe(hlr, slr), mean_epe(hrl, srl)],
+                   "epe_vs_gpu_f32": [mean_epe(hlr, g_lr), mean_epe(hrl, g_rl)],
+                   "F_u8_vs_gpu_f32": {"max_lsb": int(d32.max()), "mean_lsb": float(d32.mean()),
+                                       "frac_gt_1lsb": float((d32 > 1).mean())},
+                   "F_u8_vs_exact_oracle": {"max_lsb": int(do.max()), "mean_lsb": float(do.mean()),
+                                            "frac_gt_1lsb": float((do > 1).mean())},
+                   "meets_epe_bound": max(ex) <= 0.05}
+    return out
 
 
 def run_blend_coeff(args):
@@ -706,31 +897,21 @@ def run_refine(args):
     return 0
 
 
-def run_rig(args):
-    """The 360-degree rig: 8 RGB u8 pairs of 4000 x {800..2000}, 6 levels,
-    every step one replay of the rig's CUDA graph (luma, REDUCE, batched LK
-    per level, blend into the 9000 x 4000 canvas). The single-pair form
-    (pano_flow_pair + pano_blend_pair per pair) is timed beside it."""
-    import numpy as np
+def measure_rig(dev, pairs, pyr_dtype: str, steps: int, warmup: int, world: int = 1, autotune: bool = True,
+                single_pair: bool = True, e2e: bool = True, trace: bool = True, sample_clocks: bool = True,
+                local: int = 0):
+    """The 360-degree rig: every step one replay of the rig's CUDA graph
+    (luma, REDUCE, batched LK per level, blend into the 9000 x 4000 canvas)
+    with the strips already in HBM and L2 flushed between steps. Returns the
+    measurements and the rig (the caller closes it)."""
     import torch
 
-    rank, world, local = dist_env()
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-
-    import synth
     import paper_2006_01201_gb300 as pkg
-    from paper_2006_01201_gb300 import binding, build as gpu_build
+    from paper_2006_01201_gb300 import binding
 
-    gpu_build.build()
-    pkg.load_library()
     W = RIG_WORKLOAD
     h, widths, c, levels = W["h"], W["widths"], W["channels"], W["levels"]
-    pairs = synth.rig_pairs(h=h, widths=widths, dmax=W["dmax"], levels=levels, seed0=100 + 8 * rank)
-    pyr_code, pyr_fmt, elem = PYR_DTYPES[args.pyr_dtype]
+    pyr_code, pyr_fmt, elem = PYR_DTYPES[pyr_dtype]
     params = pkg.Params(levels=levels, iters=W["iters"], radius=W["radius"], pyr_dtype=pyr_code)
     rig = binding.Rig(params, h, widths, c=c, dtype=torch.uint8, canvas_hw=tuple(W["canvas"]),
                       canvas_x0=W["canvas_x0"])
@@ -740,180 +921,273 @@ def run_rig(args):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     npx = h * sum(widths)
+    out = {"rig": rig, "canvas": canvas, "Ls": Ls, "Rs": Rs}
 
     t0 = time.perf_counter()
-    tunings = rig.autotune(Ls, Rs, reps=3, stream=stream) if not args.no_autotune else \
+    tunings = rig.autotune(Ls, Rs, reps=3, stream=stream) if autotune else \
         [rig.get_tuning(l) for l in range(levels)]
-    tune_s = time.perf_counter() - t0
+    out["autotune"] = {"seconds": time.perf_counter() - t0 if autotune else None, "levels": tunings}
 
-    def step():
-        rig.run(Ls, Rs, canvas=canvas, use_graph=True, stream=stream)
-
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.zero_()
-        step()
+        rig.run(Ls, Rs, canvas=canvas, use_graph=True, stream=stream)
     torch.cuda.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    sampler = ClockSampler(local)
-    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    sampler = ClockSampler(local) if sample_clocks else None
+    if sampler:
+        sampler.start()
     launches0 = rig.launches
     barrier(world)
     torch.cuda.synchronize()
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
-        step()
+        rig.run(Ls, Rs, canvas=canvas, use_graph=True, stream=stream)
         ev[k][1].record(stream)
     torch.cuda.synchronize()
     barrier(world)
-    clocks = sampler.stop()
-    launches = rig.launches - launches0
-    step_ms = [a.elapsed_time(b) for a, b in ev]
+    out["clocks"] = sampler.stop() if sampler else None
+    out["launches"] = rig.launches - launches0
+    step_ms = [a_.elapsed_time(b_) for a_, b_ in ev]
     total_ms = reduce_max(sum(step_ms), world)
-    value = throughput(npx, args.steps, world, total_ms)
-
-    # --- eager runs with every launch bracketed by events: per-kernel times
-    rig.trace_enable(0x3F, 64 * args.steps)
-    for k in range(args.steps):
-        flush.zero_()
-        rig.run(Ls, Rs, canvas=canvas, use_graph=False, stream=stream)
-    torch.cuda.synchronize()
-    recs = rig.trace_read(64 * args.steps)
-    rig.trace_enable(0, 0)
-    plan = rig_level_kernels(h, widths, levels, [t["kernel"] for t in tunings],
-                             [(t["tile_w"], t["tile_h"]) for t in tunings])
-    names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "rig_blend_kernel", 16: "luma_reduce_kernel", 32: "pyr_tail_kernel"}
-    per_kind, lk_seen = {}, {}
-    stream_bytes = 0.0
-    lk_bytes = [lk_alg_bytes(h, w, levels, elem) for w in widths]
-    for kind, lev, ms in recs:
-        if kind == 4:
-            i = lk_seen.get(lev, 0) % len(plan[lev])
-            lk_seen[lev] = lk_seen.get(lev, 0) + 1
-            name, members = plan[lev][i]
-            if name == "lk_stream_batch_kernel":
-                stream_bytes += sum(lk_bytes[k][lev] for k in members)
-        else:
-            name = names[kind]
-        d = per_kind.setdefault(name, {"launches": 0, "ms": 0.0})
-        d["launches"] += 1
-        d["ms"] += ms
-    traced_total = sum(d["ms"] for d in per_kind.values())
-    for d in per_kind.values():
-        d["share"] = d["ms"] / traced_total if traced_total else None
-        d["ms_per_step"] = d["ms"] / args.steps
-    dominant = max(per_kind, key=lambda k: per_kind[k]["ms"])
-    dk = per_kind[dominant]
+    out.update(value=throughput(npx, steps, world, total_ms), ms_per_step=total_ms / steps, total_ms=total_ms,
+               step_ms_min=min(step_ms), step_ms_median=statistics.median(step_ms))
     peak, peak_src = read_peaks()
-    launch_ms = dk["ms"] / dk["launches"]
-    bytes_per_launch = stream_bytes / dk["launches"] if dominant == "lk_stream_batch_kernel" else None
-    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9 if bytes_per_launch else None
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None,
-                "traffic": TRAFFIC_PER_LAUNCH.get(dominant) if args.pyr_dtype == "f32" else None, "kernel": dominant,
-                "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
-                "launches_per_step": dk["launches"] / args.steps, "peak_source": f"{peak_src} hbm_gbs"}
-    issue = issue_roofline(dominant, launch_ms, clocks["sm_mhz"] if clocks else None) \
-        if args.pyr_dtype == "f32" else None
     path_bytes = sum(path_alg_bytes(h, w, c, levels, elem=elem) for w in widths)
+    out["path"] = {"alg_bytes_per_step": path_bytes, "alg_bytes_per_px": path_bytes / npx,
+                   "achieved_gbs": path_bytes / (total_ms / steps * 1e-3) / 1e9,
+                   "frac": path_bytes / (total_ms / steps * 1e-3) / 1e9 / peak}
 
-    def time_rig(other):
-        """CUDA-event time of K graph replays of another rig on the same strips."""
-        cv = other.new_canvas(dev)
-        for _ in range(args.warmup):
+    if trace:
+        # eager runs with every launch bracketed by events: per-kernel times
+        rig.trace_enable(0x3F, 64 * steps)
+        for k in range(steps):
             flush.zero_()
-            other.run(Ls, Rs, canvas=cv, use_graph=True, stream=stream)
+            rig.run(Ls, Rs, canvas=canvas, use_graph=False, stream=stream)
         torch.cuda.synchronize()
-        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(args.steps)]
-        for k in range(args.steps):
-            flush.zero_()
-            evs[k][0].record(stream)
-            other.run(Ls, Rs, canvas=cv, use_graph=True, stream=stream)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
-        return reduce_max(sum(a.elapsed_time(b) for a, b in evs), world), cv
+        recs = rig.trace_read(64 * steps)
+        rig.trace_enable(0, 0)
+        plan = rig_level_kernels(h, widths, levels, [t["kernel"] for t in tunings],
+                                 [(t["tile_w"], t["tile_h"]) for t in tunings])
+        names = {1: "luma_kernel", 2: "pyr_down_kernel", 8: "rig_blend_kernel", 16: "luma_reduce_kernel",
+                 32: "pyr_tail_kernel"}
+        per_kind, lk_seen = {}, {}
+        stream_bytes = 0.0
+        lk_bytes = [lk_alg_bytes(h, w, levels, elem) for w in widths]
+        for kind, lev, ms in recs:
+            if kind == 4:
+                i = lk_seen.get(lev, 0) % len(plan[lev])
+                lk_seen[lev] = lk_seen.get(lev, 0) + 1
+                name, members = plan[lev][i]
+                if name == "lk_stream_batch_kernel":
+                    stream_bytes += sum(lk_bytes[k][lev] for k in members)
+            else:
+                name = names[kind]
+            d = per_kind.setdefault(name, {"launches": 0, "ms": 0.0})
+            d["launches"] += 1
+            d["ms"] += ms
+        traced_total = sum(d["ms"] for d in per_kind.values())
+        for d in per_kind.values():
+            d["share"] = d["ms"] / traced_total if traced_total else None
+            d["ms_per_step"] = d["ms"] / steps
+        dominant = max(per_kind, key=lambda k: per_kind[k]["ms"])
+        dk = per_kind[dominant]
+        launch_ms = dk["ms"] / dk["launches"]
+        bytes_per_launch = stream_bytes / dk["launches"] if dominant == "lk_stream_batch_kernel" else None
+        achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9 if bytes_per_launch else None
+        counters = read_counters(dominant, "rig") if pyr_dtype == "f32" else None
+        out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                           "frac": achieved / peak if achieved else None,
+                           "traffic": counters["dram_bytes_per_launch"] if counters else None, "kernel": dominant,
+                           "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
+                           "launches_per_step": dk["launches"] / steps, "peak_source": f"{peak_src} hbm_gbs",
+                           "counters": "profiles/" + COUNTER_FILES[(dominant, "rig")] if counters else None}
+        clk = out["clocks"]["sm_mhz"] if out["clocks"] else None
+        out["issue_roofline"] = issue_roofline(counters, launch_ms, clk, sm_count(dev))
+        out["kernels"] = per_kind
+        out["dominant_kernel"] = dominant
 
+    if single_pair:
+        # the single-pair form on the same strips: 8 x (flow_pair + blend_pair)
+        ctx = pkg.FlowContext(params, max_h=h, max_w=max(widths), max_c=c)
+        outs = [(torch.empty((h, w, 2), device=dev), torch.empty((h, w, 2), device=dev),
+                 torch.empty_like(Ls[k])) for k, w in enumerate(widths)]
+
+        def pair_step():
+            for k in range(len(widths)):
+                ctx.flow_pair(Ls[k], Rs[k], out=outs[k][:2], stream=stream)
+                ctx.blend_pair(Ls[k], Rs[k], outs[k][0], outs[k][1], out=outs[k][2], stream=stream)
+
+        for _ in range(warmup):
+            flush.zero_()
+            pair_step()
+        torch.cuda.synchronize()
+        ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            ev3[k][0].record(stream)
+            pair_step()
+            ev3[k][1].record(stream)
+        torch.cuda.synchronize()
+        pair_ms = reduce_max(sum(a_.elapsed_time(b_) for a_, b_ in ev3), world)
+        out["single_pair_form"] = {"value": throughput(npx, steps, world, pair_ms), "unit": UNIT,
+                                   "ms_per_step": pair_ms / steps}
+        # the single-pair flows, to compare with the rig's
+        out["single_pair_flows"] = [(o[0].cpu().numpy(), o[1].cpu().numpy()) for o in outs]
+        ctx.close()
+
+    if e2e:
+        # pinned host strips in, the canvas back to pinned host memory,
+        # through the double-buffered host pipeline
+        Lh = [torch.from_numpy(p.L).pin_memory() for p in pairs]
+        Rh = [torch.from_numpy(p.R).pin_memory() for p in pairs]
+        Ch = [torch.empty(tuple(canvas.shape), dtype=canvas.dtype).pin_memory() for _ in range(2)]
+        pipe = binding.RigHostPipeline(rig, dev)
+        for k in range(max(1, warmup)):
+            pipe.submit(k, Lh, Rh, Ch[k % 2])
+        pipe.drain()
+        e2e_ms, e2e_runs = time_pipeline(pipe, lambda k: pipe.submit(k, Lh, Rh, Ch[k % 2]), steps, world)
+        out["e2e"] = {"value": throughput(npx, steps, world, e2e_ms), "unit": UNIT,
+                      "h2d_bytes_per_step": int(sum(t.numel() for t in Lh + Rh)),
+                      "d2h_bytes_per_step": int(Ch[0].numel()), "ms_per_step": e2e_ms / steps,
+                      "pipeline": "two buffer sets; H2D, graph replay and D2H on three streams; "
+                                  "no L2 flush (inputs arrive by H2D)",
+                      "repeats_ms": e2e_runs, "timing": "median of 3 timed runs of K steps"}
+        # the last replay of the pipeline wrote its canvas from the same strips
+    return out
+
+
+def mean_epe(a, b) -> float:
+    import numpy as np
+    return float(np.hypot(*(a - b).transpose(2, 0, 1)).mean())
+
+
+def rig_oracle_flows(pairs, levels: int, pyr_fmt: int = 0):
+    """FP64 oracle flows of every rig pair (storage format pyr_fmt)."""
+    import oracle
+    return [oracle.flow_pair(p.L, p.R, oracle.Params(levels=levels, pyr_fmt=pyr_fmt)) for p in pairs]
+
+
+def rig_report(dev, pairs, steps: int, warmup: int, oracle_flows=None, half: bool = True, autotune: bool = True):
+    """The rig object of the default line: the float32 rig (graph replay,
+    per-kernel times, roofline, single-pair form, end to end), the EPE of
+    every pair against the oracle and the single-pair path, and (half=True)
+    the bfloat16 and binary16 rigs with their errors."""
+    import numpy as np
+
+    W = RIG_WORKLOAD
+    levels = W["levels"]
+    m = measure_rig(dev, pairs, "f32", steps, warmup, autotune=autotune)
+    rig = m.pop("rig")
+    g32 = [tuple(t.cpu().numpy() for t in rig.flows(k)) for k in range(len(pairs))]
+    canvas32 = m.pop("canvas").cpu().numpy()
+    sp = m.pop("single_pair_flows", None)
+    Ls, Rs = m.pop("Ls"), m.pop("Rs")
+    rig.close()
+    m["npx"] = W["h"] * sum(W["widths"])
+    m["config"] = dict(W, graph=True, l2="flushed between steps (256 MB write, untimed); inputs 262 MB > L2")
+    m["epe_per_pair"] = []
+    if oracle_flows is not None:
+        for k, (lr, rl) in enumerate(g32):
+            olr, orl = oracle_flows[k]
+            row = {"pair": k, "w": W["widths"][k], "vs_oracle": [mean_epe(lr, olr), mean_epe(rl, orl)]}
+            if sp is not None:
+                row["vs_single_pair_max_abs"] = [float(np.abs(lr - sp[k][0]).max()),
+                                                 float(np.abs(rl - sp[k][1]).max())]
+            m["epe_per_pair"].append(row)
+        m["epe_vs_oracle_max_mean"] = max(max(r["vs_oracle"]) for r in m["epe_per_pair"])
+    if half:
+        m["half"] = {}
+        for dt in ("bf16", "f16"):
+            mh = measure_rig(dev, pairs, dt, steps, warmup, autotune=autotune, single_pair=False, e2e=False,
+                             trace=False, sample_clocks=False)
+            rh = mh.pop("rig")
+            gh = [tuple(t.cpu().numpy() for t in rh.flows(k)) for k in range(len(pairs))]
+            ch = mh.pop("canvas").cpu().numpy()
+            rh.close()
+            d = np.abs(ch.astype(int) - canvas32.astype(int))
+            entry = {"value": mh["value"], "unit": UNIT, "ms_per_step": mh["ms_per_step"],
+                     "fp32_value": m["value"], "canvas_u8_vs_fp32_rig": {"max_lsb": int(d.max()),
+                                                                           "mean_lsb": float(d.mean()),
+                                                                           "frac_gt_1lsb": float((d > 1).mean())},
+                     "per_pair": []}
+            _, pyr_fmt, _ = PYR_DTYPES[dt]
+            stored = rig_oracle_flows(pairs, levels, pyr_fmt) if oracle_flows is not None else None
+            for k, (lr, rl) in enumerate(gh):
+                row = {"pair": k, "vs_gpu_f32": [mean_epe(lr, g32[k][0]), mean_epe(rl, g32[k][1])]}
+                if oracle_flows is not None:
+                    row["vs_exact_oracle"] = [mean_epe(lr, oracle_flows[k][0]), mean_epe(rl, oracle_flows[k][1])]
+                    row["vs_storage_oracle"] = [mean_epe(lr, stored[k][0]), mean_epe(rl, stored[k][1])]
+                entry["per_pair"].append(row)
+            if oracle_flows is not None:
+                worst = max(max(r["vs_exact_oracle"]) for r in entry["per_pair"])
+                entry["epe_vs_exact_oracle_max_mean"] = worst
+                entry["meets_epe_bound"] = worst <= 0.05
+            m["half"][dt] = entry
+    return m
+
+
+def run_rig(args):
+    """The 360-degree rig: 8 RGB u8 pairs of 4000 x {800..2000}, 6 levels,
+    every step one replay of the rig's CUDA graph (luma, REDUCE, batched LK
+    per level, blend into the 9000 x 4000 canvas). The single-pair form
+    (pano_flow_pair + pano_blend_pair per pair) is timed beside it."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    import synth
+    W = RIG_WORKLOAD
+    h, widths, c, levels = W["h"], W["widths"], W["channels"], W["levels"]
+    # generated before the first CUDA call, in spawned processes
+    pairs = synth.rig_pairs(h=h, widths=widths, dmax=W["dmax"], levels=levels, seed0=100 + 8 * rank,
+                            workers=min(8, os.cpu_count() or 1))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_2006_01201_gb300 as pkg
+    from paper_2006_01201_gb300 import build as gpu_build
+
+    gpu_build.build()
+    pkg.load_library()
+    pyr_code, pyr_fmt, elem = PYR_DTYPES[args.pyr_dtype]
+    m = measure_rig(dev, pairs, args.pyr_dtype, args.steps, args.warmup, world=world,
+                    autotune=not args.no_autotune, local=local)
+    rig, canvas = m["rig"], m["canvas"]
     fp32_form = None
+    canvas32 = None
     if pyr_fmt:
         # the float32 batched form beside the 16-bit one, tuned the same way
-        rig32 = binding.Rig(pkg.Params(levels=levels, iters=W["iters"], radius=W["radius"]), h, widths, c=c,
-                            dtype=torch.uint8, canvas_hw=tuple(W["canvas"]), canvas_x0=W["canvas_x0"])
-        if not args.no_autotune:
-            rig32.autotune(Ls, Rs, reps=3, stream=stream)
-        ms32, canvas32 = time_rig(rig32)
-        fp32_form = {"value": throughput(npx, args.steps, world, ms32), "unit": UNIT,
-                     "ms_per_step": ms32 / args.steps}
-
-    # --- the single-pair form on the same strips: 8 x (flow_pair + blend_pair)
-    ctx = pkg.FlowContext(params, max_h=h, max_w=max(widths), max_c=c)
-    outs = [(torch.empty((h, w, 2), device=dev), torch.empty((h, w, 2), device=dev), torch.empty_like(Ls[k]))
-            for k, w in enumerate(widths)]
-
-    def pair_step():
-        for k in range(len(widths)):
-            ctx.flow_pair(Ls[k], Rs[k], out=outs[k][:2], stream=stream)
-            ctx.blend_pair(Ls[k], Rs[k], outs[k][0], outs[k][1], out=outs[k][2], stream=stream)
-
-    for _ in range(args.warmup):
-        flush.zero_()
-        pair_step()
-    torch.cuda.synchronize()
-    ev3 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    for k in range(args.steps):
-        flush.zero_()
-        ev3[k][0].record(stream)
-        pair_step()
-        ev3[k][1].record(stream)
-    torch.cuda.synchronize()
-    pair_ms = reduce_max(sum(a.elapsed_time(b) for a, b in ev3), world)
-    ctx.close()
-
-    # --- end to end: pinned host strips in, the canvas back to pinned host
-    #     memory, through the double-buffered host pipeline
-    Lh = [torch.from_numpy(p.L).pin_memory() for p in pairs]
-    Rh = [torch.from_numpy(p.R).pin_memory() for p in pairs]
-    Ch = [torch.empty(tuple(canvas.shape), dtype=canvas.dtype).pin_memory() for _ in range(2)]
-    pipe = binding.RigHostPipeline(rig, dev)
-    for k in range(max(1, args.warmup)):
-        pipe.submit(k, Lh, Rh, Ch[k % 2])
-    pipe.drain()
-    e2e_ms, e2e_runs = time_pipeline(pipe, lambda k: pipe.submit(k, Lh, Rh, Ch[k % 2]), args.steps, world)
-    e2e = {"value": throughput(npx, args.steps, world, e2e_ms), "unit": UNIT,
-           "h2d_bytes_per_step": int(sum(t.numel() for t in Lh + Rh)), "d2h_bytes_per_step": int(Ch[0].numel()),
-           "ms_per_step": e2e_ms / args.steps,
-           "pipeline": "two buffer sets; H2D, graph replay and D2H on three streams; no L2 flush (inputs arrive by H2D)",
-           "repeats_ms": e2e_runs, "timing": "median of 3 timed runs of K steps"}
+        m32 = measure_rig(dev, pairs, "f32", args.steps, args.warmup, world=world, autotune=not args.no_autotune,
+                          single_pair=False, e2e=False, trace=False, sample_clocks=False, local=local)
+        fp32_form = {"value": m32["value"], "unit": UNIT, "ms_per_step": m32["ms_per_step"]}
+        canvas32 = m32["canvas"]
+        m32["rig"].close()
 
     line = None
     if rank == 0:
         line = {"metric": METRIC.replace("(bi-flow+warp+blend)", "(bi-flow+warp+blend, 8-pair rig)"),
-                "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+                "value": m["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": dict(W, l2="flushed between steps (256 MB write, untimed); inputs 262 MB > L2",
                                parallelism=f"replicas{world}", graph=True, pyr_dtype=args.pyr_dtype),
-                "roofline": roofline, "issue_roofline": issue,
-                "path": {"alg_bytes_per_step": path_bytes,
-                         "achieved_gbs": path_bytes / (total_ms / args.steps * 1e-3) / 1e9},
-                "kernels": per_kind, "dominant_kernel": dominant,
-                "single_pair_form": {"value": throughput(npx, args.steps, world, pair_ms), "unit": UNIT,
-                                     "ms_per_step": pair_ms / args.steps},
-                "fp32_batched_form": fp32_form,
-                "paper_context": PAPER_CONTEXT,
-                "autotune": {"seconds": tune_s, "levels": tunings},
-                "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
-                "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}
+                "roofline": m["roofline"], "issue_roofline": m["issue_roofline"], "path": m["path"],
+                "kernels": m["kernels"], "dominant_kernel": m["dominant_kernel"],
+                "single_pair_form": m["single_pair_form"], "fp32_batched_form": fp32_form,
+                "paper_context": PAPER_CONTEXT, "autotune": m["autotune"],
+                "e2e": m["e2e"], "gpu_launches": m["launches"], "clocks": m["clocks"],
+                "step_ms_min": m["step_ms_min"], "step_ms_median": m["step_ms_median"]}
         if world == 1 and not args.no_cpu_baseline:
             import oracle
             oracle.build()
             olr, orl = oracle.flow_pair(pairs[0].L, pairs[0].R, oracle.Params(levels=levels))
             g_lr, g_rl = (t.cpu().numpy() for t in rig.flows(0))
-            line["epe_vs_oracle"] = {
-                "pair": 0,
-                "LtoR_mean_px": float(np.hypot(*(g_lr - olr).transpose(2, 0, 1)).mean()),
-                "RtoL_mean_px": float(np.hypot(*(g_rl - orl).transpose(2, 0, 1)).mean())}
+            line["epe_vs_oracle"] = {"pair": 0, "LtoR_mean_px": mean_epe(g_lr, olr),
+                                     "RtoL_mean_px": mean_epe(g_rl, orl)}
             if pyr_fmt:
                 # pair 1 owns its whole canvas span (columns 1125 .. 2074): pair 0's
                 # first columns are overwritten by pair 7, which wraps around the seam
@@ -928,7 +1202,7 @@ def run_rig(args):
                     "max_lsb": int((canvas.int() - canvas32.int()).abs().max()),
                     "mean_lsb": float((canvas.int() - canvas32.int()).abs().float().mean())}
             line["cpu_baseline"] = oracle_baseline(pairs[0], levels, args.cpu_budget, "of rig pair 0 (4000x800)")
-            line["cpu_baseline"]["rig_step_s_extrapolated"] = npx / 1e6 / line["cpu_baseline"]["value"]
+            line["cpu_baseline"]["rig_step_s_extrapolated"] = h * sum(widths) / 1e6 / line["cpu_baseline"]["value"]
     if rank == 0:
         print(json.dumps(line), flush=True)
     rig.close()
@@ -1032,11 +1306,22 @@ def main(argv=None):
                          "rig: the 8-pair 360-degree rig; refine_1024: the differentiable refinement; "
                          "blend_coeff: general-mask Eq. (1); compose: Code 1 on a 4000x3000 canvas")
     ap.add_argument("--no-autotune", action="store_true", help="rig: keep the default tuning")
+    ap.add_argument("--no-rig", action="store_true",
+                    help="pair: leave out the rig and the 16-bit forms that the default line carries")
+    ap.add_argument("--ingest-ncu", metavar="CSV",
+                    help="write the profiles/ counters of --counters-kernel from an `ncu -i REPORT --page raw "
+                         "--csv` export (no GPU needed) and exit")
+    ap.add_argument("--counters-kernel", default="lk_stream_kernel")
+    ap.add_argument("--counters-workload", default=WORKLOAD["workload"])
+    ap.add_argument("--counters-command", default="", help="the capture command, recorded with the counters")
     ap.add_argument("--pyr-dtype", default="f32", choices=sorted(PYR_DTYPES),
                     help="storage of the pyramid levels (arithmetic stays FP32)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.ingest_ncu:
+        print(ingest_ncu(args.ingest_ncu, args.counters_kernel, args.counters_workload, args.counters_command))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "refine_1024":

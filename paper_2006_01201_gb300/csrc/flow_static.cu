@@ -13,8 +13,6 @@
 // of PANO_STATIC_SCRATCH_BYTES instead. Every GPU that loads the library
 // holds the array until the process exits. The kernels are the ones
 // pano_flow_pair launches; only where their scratch lives differs.
-#include <stdarg.h>
-#include <stdio.h>
 #include <string.h>
 
 #include <mutex>
@@ -35,60 +33,28 @@ constexpr int kMaxDevices = 64;
 struct DeviceSetup {
     bool done = false;
     unsigned char* scratch = nullptr;  // device address of g_static_scratch
-    int max_smem = 0;
 };
 DeviceSetup g_setup[kMaxDevices];
 std::mutex g_setup_mutex;
 
-pano_status sfail(pano_status st, const char* fmt, ...) {
-    char msg[512];
-    va_list ap;
-    va_start(ap, fmt);
-    vsnprintf(msg, sizeof(msg), fmt, ap);
-    va_end(ap);
-    set_last_error(msg);
-    return st;
-}
-
 // Once per device, with that device current: the device address of the
-// scratch array (host code cannot use the symbol itself) and the kernel's
-// dynamic shared-memory limit.
+// scratch array (host code cannot use the symbol itself). The kernels'
+// shared-memory limits are set by ensure_lk_ready, as for a context.
 pano_status setup_current_device(DeviceSetup** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return sfail(PANO_ERR_CUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return sfail(PANO_ERR_UNSUPPORTED, "device index %d", dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kMaxDevices) return fail(PANO_ERR_UNSUPPORTED, "device index %d", dev);
     std::lock_guard<std::mutex> lock(g_setup_mutex);
     DeviceSetup& s = g_setup[dev];
     if (!s.done) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess)
-            return sfail(PANO_ERR_CUDA, "cudaGetSymbolAddress(scratch): %s", cudaGetErrorString(e));
-        int ms = 0;
-        e = cudaDeviceGetAttribute(&ms, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        if (e != cudaSuccess) return sfail(PANO_ERR_CUDA, "shared-memory limit: %s", cudaGetErrorString(e));
-        e = lk_prepare(ms);
-        if (e != cudaSuccess) return sfail(PANO_ERR_CUDA, "cudaFuncSetAttribute: %s", cudaGetErrorString(e));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
         s.scratch = static_cast<unsigned char*>(p);
-        s.max_smem = ms;
         s.done = true;
     }
     *out = &s;
-    return PANO_OK;
-}
-
-pano_status check_img(const pano_image* im, const char* name) {
-    if (!im || !im->data) return sfail(PANO_ERR_INVALID_ARG, "%s is NULL", name);
-    if (im->h < 1 || im->w < 1) return sfail(PANO_ERR_INVALID_ARG, "%s size %dx%d", name, im->h, im->w);
-    if (im->dtype != PANO_U8 && im->dtype != PANO_F32)
-        return sfail(PANO_ERR_UNSUPPORTED, "%s: dtype %d (PANO_U8 or PANO_F32)", name, im->dtype);
-    if (im->c != 1 && im->c != 3) return sfail(PANO_ERR_UNSUPPORTED, "%s: %d channels", name, im->c);
-    size_t es = im->dtype == PANO_U8 ? 1 : 4;
-    if (im->pitch_bytes < (size_t)im->w * im->c * es || im->pitch_bytes % es || ((uintptr_t)im->data) % es)
-        return sfail(PANO_ERR_INVALID_ARG, "%s: bad pitch or alignment", name);
-    if ((double)im->h * (double)(im->pitch_bytes / es) > 2147483647.0)
-        return sfail(PANO_ERR_UNSUPPORTED, "%s: more than 2^31 elements", name);
     return PANO_OK;
 }
 
@@ -113,34 +79,33 @@ extern "C" {
 
 pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L, const pano_image* R,
                                   float* flow_LtoR, float* flow_RtoL, void* cuda_stream) {
-    if (!p) return sfail(PANO_ERR_INVALID_ARG, "params is NULL");
-    if (p->levels < 1 || p->levels > kMaxLevels || p->iters < 0 || p->iters > 16 || p->radius < 1 ||
-        p->radius > 3 || !(p->lambda >= 0.f) || !(p->lambda < 1e30f))
-        return sfail(PANO_ERR_INVALID_ARG, "parameters out of range");
-    if (p->pyr_dtype != PANO_F32) return sfail(PANO_ERR_UNSUPPORTED, "pyramid dtype %d", p->pyr_dtype);
+    // the argument checks of pano_flow_pair, except that there is no
+    // context: its maximum sizes are replaced by the size of the scratch
     pano_status st;
-    if ((st = check_img(L, "L")) != PANO_OK) return st;
-    if ((st = check_img(R, "R")) != PANO_OK) return st;
-    if (L->h != R->h || L->w != R->w || L->c != R->c || L->dtype != R->dtype)
-        return sfail(PANO_ERR_INVALID_ARG, "L and R differ in size, channels or dtype");
-    if (!flow_LtoR || !flow_RtoL || ((uintptr_t)flow_LtoR) % 8 || ((uintptr_t)flow_RtoL) % 8)
-        return sfail(PANO_ERR_INVALID_ARG, "flows must be non-NULL and 8-byte aligned");
+    if ((st = check_params(p)) != PANO_OK) return st;
+    if (p->pyr_dtype != PANO_F32)
+        return fail(PANO_ERR_UNSUPPORTED, "pyramid dtype %d: this entry point keeps float32 pyramids", p->pyr_dtype);
+    if ((st = check_image(L, "L")) != PANO_OK) return st;
+    if ((st = check_image(R, "R")) != PANO_OK) return st;
+    if ((st = check_same(L, R, "L", "R")) != PANO_OK) return st;
+    if ((st = check_flow(flow_LtoR, "flow_LtoR")) != PANO_OK) return st;
+    if ((st = check_flow(flow_RtoL, "flow_RtoL")) != PANO_OK) return st;
+    const size_t fbytes = (size_t)L->h * L->w * 2 * sizeof(float);
+    if (overlaps(flow_LtoR, fbytes, flow_RtoL, fbytes)) return fail(PANO_ERR_INVALID_ARG, "the two flows overlap");
     const size_t need = static_scratch_bytes(L->h, L->w, p->levels);
     if (need > (size_t)PANO_STATIC_SCRATCH_BYTES)
-        return sfail(PANO_ERR_INVALID_ARG,
-                     "strip %dx%d with %d levels needs %zu bytes of scratch; the fixed scratch holds %zu",
-                     L->h, L->w, p->levels, need, (size_t)PANO_STATIC_SCRATCH_BYTES);
+        return fail(PANO_ERR_INVALID_ARG,
+                    "strip %dx%d with %d levels needs %zu bytes of scratch; the fixed scratch holds %zu", L->h,
+                    L->w, p->levels, need, (size_t)PANO_STATIC_SCRATCH_BYTES);
+    int max_smem = 0;
+    if ((st = ensure_lk_ready(&max_smem)) != PANO_OK) return st;
     DeviceSetup* ds = nullptr;
     if ((st = setup_current_device(&ds)) != PANO_OK) return st;
-    static const int cand[][2] = {{32, 16}, {32, 8}, {16, 16}, {16, 8}, {8, 8}};
     int tw = 0, th = 0;
-    for (auto& c : cand)
-        if (lk_smem_bytes(c[0], c[1], p->iters, p->radius) <= (size_t)ds->max_smem) {
-            tw = c[0];
-            th = c[1];
-            break;
-        }
-    if (!tw) return sfail(PANO_ERR_UNSUPPORTED, "iters * radius too large for shared memory");
+    if (!pick_tile(p->iters, p->radius, max_smem, &tw, &th))
+        return fail(PANO_ERR_UNSUPPORTED, "iters * radius = %d needs more shared memory than the device has",
+                    p->iters * p->radius);
+    NvtxRange range("pano_flow_pair_static");
 
     // Carve the fixed scratch exactly as static_scratch_bytes counts it.
     const int nlev = p->levels;
@@ -171,23 +136,18 @@ pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L
     int ppitch[2][kMaxLevels];
     LumaArgs la;
     memset(&la, 0, sizeof(la));
+    la.pyr = kPyrF32;
     for (int si = 0; si < 2; ++si) {
         for (int l = 0; l < nlev; ++l) {
             plane[si][l] = pyr[si][l];
             ppitch[si][l] = lp[l];
         }
         if (img[si]->dtype == PANO_F32 && img[si]->c == 1) {
+            // a one-channel float strip is its own luma
             plane[si][0] = static_cast<const float*>(img[si]->data);
             ppitch[si][0] = (int)(img[si]->pitch_bytes / sizeof(float));
         } else {
-            ImageDesc d;
-            d.data = img[si]->data;
-            d.h = img[si]->h;
-            d.w = img[si]->w;
-            d.c = img[si]->c;
-            d.pitch_bytes = (long long)img[si]->pitch_bytes;
-            d.dtype = img[si]->dtype == PANO_U8 ? 0 : 1;
-            la.in[la.count] = d;
+            la.in[la.count] = desc(img[si]);
             la.out[la.count] = pyr[si][0];
             la.out_pitch[la.count] = lp[0];
             la.count++;
@@ -207,11 +167,11 @@ pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L
             lr.l1_pitch[i] = lp[1];
         }
         lr.count = 2;
-        if ((e = launch_luma_reduce(lr, s)) != cudaSuccess)
-            return sfail(PANO_ERR_CUDA, "luma launch: %s", cudaGetErrorString(e));
+        lr.pyr = kPyrF32;
+        if ((e = launch_luma_reduce(lr, s)) != cudaSuccess) return cuda_fail(e, "luma launch");
         first = 2;
     } else if (la.count > 0 && (e = launch_luma(la, s)) != cudaSuccess) {
-        return sfail(PANO_ERR_CUDA, "luma launch: %s", cudaGetErrorString(e));
+        return cuda_fail(e, "luma launch");
     }
     {
         // the other levels (the same launch sequence as pano_flow_pair)
@@ -227,10 +187,12 @@ pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L
         }
         ps.count = 2;
         ps.nlev = nlev;
+        ps.pyr = kPyrF32;
         int kernels = 0;
         if ((e = launch_pyramid_rest(ps, first, nullptr, s, &kernels)) != cudaSuccess)
-            return sfail(PANO_ERR_CUDA, "pyramid launch: %s", cudaGetErrorString(e));
+            return cuda_fail(e, "pyramid launch");
     }
+    if ((e = debug_check(s)) != cudaSuccess) return cuda_fail(e, "pyramid (PANO_DEBUG=sync)");
     float* out[2] = {flow_LtoR, flow_RtoL};
     for (int l = nlev - 1; l >= 0; --l) {
         LkArgs ka;
@@ -253,9 +215,10 @@ pano_status pano_flow_pair_static(const pano_flow_params* p, const pano_image* L
         ka.iters = p->iters;
         ka.radius = p->radius;
         ka.lambda = p->lambda;
+        ka.pyr = kPyrF32;
         lk_level_tile(ka.w, ka.h, tw, th, &ka.tile_w, &ka.tile_h);  // as pano_flow_pair
-        if ((e = launch_lk_level(ka, 2, s)) != cudaSuccess)
-            return sfail(PANO_ERR_CUDA, "LK launch: %s", cudaGetErrorString(e));
+        if ((e = launch_lk_level(ka, 2, s)) != cudaSuccess) return cuda_fail(e, "LK launch");
+        if ((e = debug_check(s)) != cudaSuccess) return cuda_fail(e, "LK level (PANO_DEBUG=sync)");
     }
     return PANO_OK;
 }

@@ -225,8 +225,30 @@ def pair_translation(dx: float, dy: float, seed: int = 5, h: int = 96, w: int = 
                      meta={"field": "translation", "dx": dx, "dy": dy})
 
 
+def _rig_pair_arrays(args):
+    """Worker of rig_pairs: the arrays of one pair (the field closure stays
+    behind; the parent rebuilds it from the same seed)."""
+    seed, h, w, dmax, levels = args
+    p = pair_fullres_rgb(seed=seed, h=h, w=w, dmax=dmax, levels=levels)
+    return p.name, p.L, p.R, p.flow_RtoL, p.meta
+
+
 def rig_pairs(h: int = 4000, widths=RIG_WIDTHS, dmax: float = 24.0, levels: int = 6,
-              seed0: int = 100) -> list:
-    """Eight overlap pairs of a 360-degree rig with uneven widths."""
-    return [pair_fullres_rgb(seed=seed0 + k, h=h, w=wk, dmax=dmax, levels=levels)
-            for k, wk in enumerate(widths)]
+              seed0: int = 100, workers: int = 1) -> list:
+    """Eight overlap pairs of a 360-degree rig with uneven widths.
+
+    workers > 1 generates the pairs in that many processes (started with
+    ``spawn``, so it is safe in a process that already uses a GPU); the pairs
+    are the same as with one worker."""
+    jobs = [(seed0 + k, h, wk, dmax, levels) for k, wk in enumerate(widths)]
+    if workers <= 1:
+        return [pair_fullres_rgb(seed=s, h=hh, w=ww, dmax=d, levels=lv) for s, hh, ww, d, lv in jobs]
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(max_workers=min(workers, len(jobs)), mp_context=mp.get_context("spawn")) as ex:
+        arrays = list(ex.map(_rig_pair_arrays, jobs))
+    out = []
+    for (seed, hh, ww, d, lv), (name, L, R, flow, meta) in zip(jobs, arrays):
+        dfun = _parallax_field(np.random.default_rng(10_000 + seed), hh, ww, d)
+        out.append(Pair(name=name, L=L, R=R, flow_RtoL=flow, dfun=dfun, levels=lv, meta=meta))
+    return out

@@ -201,3 +201,36 @@ def test_rig_null_arguments(lib):
     assert lib.pano_rig_set_tuning(None, 0, ctypes.byref(t)) == binding.PANO_ERR_INVALID_ARG
     assert lib.pano_rig_destroy(None) == binding.PANO_OK
     assert lib.pano_rig_launches(None) == 0 and lib.pano_rig_graph_captures(None) == 0
+
+
+def test_static_flow_rejects_bad_arguments_before_any_device_call(lib):
+    """pano_flow_pair_static runs the checks of pano_flow_pair (parameters,
+    images, flows that must not overlap) before it touches the device."""
+    inv = binding.PANO_ERR_INVALID_ARG
+    p = binding.PanoParams()
+    lib.pano_flow_params_default(ctypes.byref(p))
+    img = binding.PanoImage(0x100000, 64, 64, 1, 256, binding.PANO_F32)
+    n = 64 * 64 * 8
+
+    def call(q=p, L=img, R=img, lr=0x200000, rl=0x200000 + n):
+        return lib.pano_flow_pair_static(ctypes.byref(q) if q is not None else None, ctypes.byref(L),
+                                         ctypes.byref(R), lr, rl, None)
+
+    assert call(q=None) == inv
+    assert call(rl=0x200000 + n - 8) == inv            # the two flows overlap by one pixel
+    assert b"overlap" in lib.pano_last_error(None)
+    assert call(lr=0x200004) == inv                    # not 8-byte aligned
+    assert call(R=binding.PanoImage(0x100000, 64, 63, 1, 256, binding.PANO_F32)) == inv
+    for field, value in (("soft_sharpness", float("nan")), ("flow_mag_coef", float("nan")), ("levels", 13),
+                         ("radius", 4), ("lam", -1.0)):
+        q = binding.PanoParams()
+        lib.pano_flow_params_default(ctypes.byref(q))
+        setattr(q, field, value)
+        assert call(q=q) == inv, field
+    q = binding.PanoParams()
+    lib.pano_flow_params_default(ctypes.byref(q))
+    q.pyr_dtype = binding.PANO_BF16
+    assert call(q=q) == binding.PANO_ERR_UNSUPPORTED
+    big = binding.PanoImage(0x100000, 2048, 2048, 1, 8192, binding.PANO_F32)
+    assert call(L=big, R=big, rl=0x200000 + 2048 * 2048 * 8) == inv
+    assert b"scratch" in lib.pano_last_error(None)

@@ -18,14 +18,54 @@ def test_level_pixels_and_lk_bytes():
 
 def test_issue_roofline_against_the_schedulers_peak():
     # 1.2587e11 warp instructions per second = 152 SMs x 4 schedulers x 2070 MHz / 10
-    inst = bench.INST_PER_LAUNCH["lk_stream_kernel"]
-    launch_ms = inst / (0.1 * 152 * 4 * 2070e6) * 1e3
-    r = bench.issue_roofline("lk_stream_kernel", launch_ms, 2070.0)
+    counters = {"kernel": "lk_stream_kernel", "workload": "pair_4000x1500_rgb_u8_lv6",
+                "warp_inst_per_launch": 125.5e6}
+    launch_ms = 125.5e6 / (0.1 * 152 * 4 * 2070e6) * 1e3
+    r = bench.issue_roofline(counters, launch_ms, 2070.0, 152)
     assert r["peak"] == pytest.approx(152 * 4 * 2.07)
     assert r["frac"] == pytest.approx(0.1)
-    # no instruction count, no clock sample: no figure
-    assert bench.issue_roofline("blend_kernel", 1.0, 2070.0) is None
-    assert bench.issue_roofline("lk_stream_kernel", 1.0, None) is None
+    # no counters, no clock sample: no figure
+    assert bench.issue_roofline(None, 1.0, 2070.0, 152) is None
+    assert bench.issue_roofline(counters, 1.0, None, 152) is None
+
+
+def test_path_bytes_follow_the_per_pixel_model():
+    # 4000x1500 RGB u8, 6 levels: strips 6 B, luma levels 8 S, flow 36 S (minus the
+    # coarsest level's missing coarse read), blend 25 B: about 90 B per pixel
+    n = 4000 * 1500
+    b = bench.path_alg_bytes(4000, 1500, 3, 6)
+    assert 89.0 < b / n < 90.0
+    # the REDUCE re-read model adds 8 B per pixel of levels 0-4
+    rr = bench.path_alg_bytes(4000, 1500, 3, 6, reduce_reread=True)
+    assert rr - b == 8 * sum(bench.level_pixels(4000, 1500, 6)[:-1])
+    # a one-channel float strip is its own level 0: no level-0 write
+    g = bench.path_alg_bytes(256, 512, 1, 4, in_bytes=4)
+    npx = bench.level_pixels(256, 512, 4)
+    assert g == 2 * 4 * 256 * 512 + 8 * sum(npx[1:]) + sum(bench.lk_alg_bytes(256, 512, 4)) + 28 * 256 * 512
+
+
+def test_ncu_counters_round_trip_and_go_stale_with_the_source(tmp_path, monkeypatch):
+    csv = tmp_path / "raw.csv"
+    csv.write_text(
+        '"ID","Kernel Name","dram__bytes_read.sum","dram__bytes_write.sum","smsp__inst_executed.sum",'
+        '"gpu__time_duration.sum"\n'
+        '"","","Mbyte","Kbyte","inst","nsecond"\n'
+        '"0","lk_stream_kernel<2, 5, 96, 12, float>","110.5","2,000","368200597","623600"\n'
+        '"1","blend_kernel<unsigned char, 3>","1","1","1","1"\n'
+        '"2","lk_stream_kernel<2, 5, 96, 12, float>","18.5","0","90773349","172300"\n')
+    rows = bench.parse_ncu_raw_csv(str(csv), "lk_stream_kernel")
+    assert len(rows) == 2
+    assert rows[0]["dram_bytes"] == pytest.approx(110.5e6 + 2e6)
+    assert rows[1]["warp_inst"] == 90773349
+    out = bench.ingest_ncu(str(csv), "lk_stream_kernel", "pair_4000x1500_rgb_u8_lv6", "cmd",
+                           profiles_dir=str(tmp_path))
+    assert os.path.exists(out)
+    c = bench.read_counters("lk_stream_kernel", "pair_4000x1500_rgb_u8_lv6", profiles_dir=str(tmp_path))
+    assert c["dram_bytes_per_launch"] == pytest.approx((112.5e6 + 18.5e6) / 2)
+    assert c["warp_inst_per_launch"] == pytest.approx((368200597 + 90773349) / 2)
+    # the kernel's sources change: the counters no longer apply
+    monkeypatch.setattr(bench, "source_digest", lambda files: "0" * 64)
+    assert bench.read_counters("lk_stream_kernel", "pair_4000x1500_rgb_u8_lv6", profiles_dir=str(tmp_path)) is None
 
 
 def test_throughput_counts_every_rank():

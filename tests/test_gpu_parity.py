@@ -6,7 +6,8 @@ Stage tests feed the GPU and the oracle the same inputs. Tolerances:
   * one LK step: max-abs 1e-4 px;
   * Code 1 blend on identical flows: f32 max-abs 1e-5, u8 within 1 LSB
     (a value within FP32 rounding of a .5 tie may round either way);
-  * end to end: mean endpoint error <= 0.05 px per direction.
+  * end to end: mean endpoint error <= 0.05 px per direction, and every
+    pixel of F within 1/255 of the oracle's whole path (u8: one level).
 """
 import numpy as np
 import pytest
@@ -255,6 +256,13 @@ def _e2e(pair, check_blend_u8=True):
         assert np.abs(F.astype(int) - oracle.quantize_u8(Fo).astype(int)).max() <= 1
     else:
         assert np.abs(F - Fo).max() <= 1e-5
+    # the whole path against the whole oracle path (its own flows, then Code 1):
+    # every blended pixel within 1/255 (u8: one level)
+    Fw = oracle.blend(pair.L, pair.R, olr, orl, P)
+    if pair.L.dtype == np.uint8:
+        assert np.abs(F.astype(int) - oracle.quantize_u8(Fw).astype(int)).max() <= 1
+    else:
+        assert np.abs(F - Fw).max() <= 1.0 / 255
     return e_lr, e_rl, F, olr, orl
 
 
@@ -264,7 +272,7 @@ def test_end_to_end_small_gray_pair():
     # whole path against the whole oracle path: flows and F
     Fo = oracle.blend(pair.L, pair.R, olr, orl, oracle.Params(levels=pair.levels))
     d = np.abs(F - Fo)
-    assert d.mean() <= 1e-4 and np.percentile(d, 99.9) <= 1.0 / 255
+    assert d.mean() <= 1e-4 and d.max() <= 1.0 / 255
 
 
 @pytest.mark.parametrize("h,w,c,levels", [(1, 1, 1, 1), (2, 3, 3, 3), (5, 7, 1, 4), (33, 65, 3, 3),
@@ -340,4 +348,4 @@ def test_full_size_rgb_pair_matches_oracle():
     e_lr, e_rl, F, olr, orl = _e2e(pair)
     Fo = oracle.quantize_u8(oracle.blend(pair.L, pair.R, olr, orl, oracle.Params(levels=6)))
     d = np.abs(F.astype(int) - Fo.astype(int))
-    assert d.mean() <= 0.05
+    assert d.mean() <= 0.05 and d.max() <= 1

@@ -102,3 +102,43 @@ def test_strip_too_large_for_the_fixed_scratch_is_refused():
     assert ei.value.status == binding.PANO_ERR_INVALID_ARG
     assert "scratch" in ei.value.message
     assert np.isfinite(big.sum().item())
+
+
+_FRESH = r"""
+import sys
+import numpy as np
+import torch
+sys.path.insert(0, {root!r})
+import synth
+from paper_2006_01201_gb300 import binding
+binding.load_library()
+dev = torch.device("cuda:0")
+pair = synth.pair_fullres_rgb(seed=9, h=520, w=700, dmax=10.0, levels=7)
+L = torch.from_numpy(pair.L).to(dev)
+R = torch.from_numpy(pair.R).to(dev)
+worst = 0.0
+for levels in (6, 7):
+    p = binding.Params(levels=levels)
+    s_lr, s_rl = binding.flow_pair_static(p, L, R)   # before any context exists
+    torch.cuda.synchronize()
+    with binding.FlowContext(p, max_h=520, max_w=700, max_c=3) as ctx:
+        c_lr, c_rl = ctx.flow_pair(L, R)
+        torch.cuda.synchronize()
+    worst = max(worst, (s_lr - c_lr).abs().max().item(), (s_rl - c_rl).abs().max().item())
+print("MAXDIFF", worst)
+"""
+
+
+def test_static_flow_with_six_and_seven_levels_in_a_fresh_process():
+    """With 6 or more levels the pyramid's multi-level REDUCE needs more than
+    48 KB of shared memory; the first call of a process that never created a
+    context must set that limit itself."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _FRESH.format(root=root)], capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stdout + r.stderr
+    worst = float(r.stdout.split("MAXDIFF")[1].split()[0])
+    assert worst <= MAX_ABS, worst
