@@ -146,7 +146,8 @@ def _unit_scale(unit: str) -> float:
 
 def parse_ncu_raw_csv(path: str, kernel: str):
     """Per-launch DRAM bytes, warp instructions and durations of the launches
-    of `kernel` (name prefix) in an `ncu -i REPORT --page raw --csv` export."""
+    of `kernel` (its name, as a whole word before the template or parameter
+    list) in an `ncu -i REPORT --page raw --csv` export."""
     import csv
     with open(path, newline="") as f:
         rows = list(csv.reader(f))
@@ -160,9 +161,11 @@ def parse_ncu_raw_csv(path: str, kernel: str):
             return None
         return float(r[i].replace(",", "")) * _unit_scale(units[i])
 
+    import re
+    pat = re.compile(r"(^|[\s:])" + re.escape(kernel) + r"[<(]")
     out = []
     for r in rows[hi + 2:]:
-        if len(r) <= col["Kernel Name"] or not r[col["Kernel Name"]].startswith(kernel):
+        if len(r) <= col["Kernel Name"] or not pat.search(r[col["Kernel Name"]]):
             continue
         rd, wr = val(r, "dram__bytes_read.sum"), val(r, "dram__bytes_write.sum")
         out.append({"name": r[col["Kernel Name"]],
@@ -172,10 +175,14 @@ def parse_ncu_raw_csv(path: str, kernel: str):
     return out
 
 
-def ingest_ncu(csv_path: str, kernel: str, workload: str, command: str, profiles_dir: str = None) -> str:
+def ingest_ncu(csv_path: str, kernel: str, workload: str, command: str, profiles_dir: str = None,
+               first: int = 0, count: int = 0, tuning=None) -> str:
     """Write profiles/<counters file> for (kernel, workload) from an ncu raw
-    CSV export, stamped with the digest of the kernel's current sources."""
+    CSV export (its launches first .. first + count - 1, all with count 0),
+    stamped with the digest of the kernel's current sources. `tuning`
+    records the rig tuning the capture ran with, if any."""
     launches = parse_ncu_raw_csv(csv_path, kernel)
+    launches = launches[first:first + count] if count else launches[first:]
     if not launches:
         raise SystemExit(f"no launch of {kernel} in {csv_path}")
 
@@ -186,6 +193,8 @@ def ingest_ncu(csv_path: str, kernel: str, workload: str, command: str, profiles
     d = {"kernel": kernel, "workload": workload, "sources": KERNEL_SOURCES[kernel],
          "sha256": source_digest(KERNEL_SOURCES[kernel]), "command": command, "launches": launches,
          "dram_bytes_per_launch": mean("dram_bytes"), "warp_inst_per_launch": mean("warp_inst")}
+    if tuning is not None:
+        d["tuning"] = tuning
     path = os.path.join(profiles_dir or os.path.join(ROOT, "profiles"), COUNTER_FILES[(kernel, workload)])
     with open(path, "w") as f:
         json.dump(d, f, indent=1)
@@ -203,6 +212,12 @@ RIG_WORKLOAD = {"workload": "rig_8x4000x{800..2000}_rgb_u8_lv6_canvas_9000x4000"
                 "iters": 5, "radius": 2, "dmax": 24.0, "canvas": [4000, 9000],
                 "canvas_x0": [1125 * k for k in range(8)]}
 PANO_LK_AUTO, PANO_LK_STREAM, PANO_LK_TILE = 0, 1, 2
+# a rig level's tuning as (kernel, seg_rows, tile_w, tile_h); the default is AUTO everywhere
+DEFAULT_TUNING = [PANO_LK_AUTO, 0, 0, 0]
+
+
+def tuning_key(t) -> list:
+    return [int(t["kernel"]), int(t["seg_rows"]), int(t["tile_w"]), int(t["tile_h"])]
 # --pyr-dtype: (pano_dtype of the pyramid storage, oracle storage format, bytes per stored element)
 PYR_DTYPES = {"f32": (1, 0, 4), "bf16": (2, 1, 2), "f16": (3, 2, 2)}
 
@@ -996,8 +1011,12 @@ def measure_rig(dev, pairs, pyr_dtype: str, steps: int, warmup: int, world: int 
         bytes_per_launch = stream_bytes / dk["launches"] if dominant == "lk_stream_batch_kernel" else None
         achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9 if bytes_per_launch else None
         counters = read_counters(dominant, "rig") if pyr_dtype == "f32" else None
+        note = None
+        if counters and counters.get("tuning") != [tuning_key(t) for t in tunings]:
+            # taken with another tuning: other launches, other counts
+            counters, note = None, "counters were captured with another tuning"
         out["roofline"] = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                           "frac": achieved / peak if achieved else None,
+                           "frac": achieved / peak if achieved else None, "counters_note": note,
                            "traffic": counters["dram_bytes_per_launch"] if counters else None, "kernel": dominant,
                            "alg_bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                            "launches_per_step": dk["launches"] / steps, "peak_source": f"{peak_src} hbm_gbs",
@@ -1084,6 +1103,15 @@ def rig_report(dev, pairs, steps: int, warmup: int, oracle_flows=None, half: boo
     sp = m.pop("single_pair_flows", None)
     Ls, Rs = m.pop("Ls"), m.pop("Rs")
     rig.close()
+    if autotune:
+        # the same rig with the default tuning of every level: the tuning the
+        # committed ncu counters of the batch kernel were captured with
+        md = measure_rig(dev, pairs, "f32", steps, warmup, autotune=False, single_pair=False, e2e=False,
+                         sample_clocks=True)
+        md.pop("rig").close()
+        m["default_tuning"] = {k: md[k] for k in ("value", "ms_per_step", "roofline", "issue_roofline", "kernels",
+                                                  "dominant_kernel", "clocks")}
+        m["default_tuning"]["unit"] = UNIT
     m["npx"] = W["h"] * sum(W["widths"])
     m["config"] = dict(W, graph=True, l2="flushed between steps (256 MB write, untimed); inputs 262 MB > L2")
     m["epe_per_pair"] = []
@@ -1324,13 +1352,19 @@ def main(argv=None):
     ap.add_argument("--counters-kernel", default="lk_stream_kernel")
     ap.add_argument("--counters-workload", default=WORKLOAD["workload"])
     ap.add_argument("--counters-command", default="", help="the capture command, recorded with the counters")
+    ap.add_argument("--counters-launches", default="0:0", help="first:count of the captured launches to keep")
+    ap.add_argument("--counters-default-tuning", action="store_true",
+                    help="record that the rig ran with the default tuning of every level")
     ap.add_argument("--pyr-dtype", default="f32", choices=sorted(PYR_DTYPES),
                     help="storage of the pyramid levels (arithmetic stays FP32)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.ingest_ncu:
-        print(ingest_ncu(args.ingest_ncu, args.counters_kernel, args.counters_workload, args.counters_command))
+        first, count = (int(v) for v in args.counters_launches.split(":"))
+        tuning = [DEFAULT_TUNING] * RIG_WORKLOAD["levels"] if args.counters_default_tuning else None
+        print(ingest_ncu(args.ingest_ncu, args.counters_kernel, args.counters_workload, args.counters_command,
+                         first=first, count=count, tuning=tuning))
         return 0
     if args.impl == "reference":
         return run_reference(args)

@@ -50,8 +50,8 @@ def test_ncu_counters_round_trip_and_go_stale_with_the_source(tmp_path, monkeypa
         '"ID","Kernel Name","dram__bytes_read.sum","dram__bytes_write.sum","smsp__inst_executed.sum",'
         '"gpu__time_duration.sum"\n'
         '"","","Mbyte","Kbyte","inst","nsecond"\n'
-        '"0","lk_stream_kernel<2, 5, 96, 12, float>","110.5","2,000","368200597","623600"\n'
-        '"1","blend_kernel<unsigned char, 3>","1","1","1","1"\n'
+        '"0","void lk_stream_kernel<2, 5, 96, 12, float>(LkArgs, int)","110.5","2,000","368200597","623600"\n'
+        '"1","void lk_stream_batch_kernel<2, 5, 96, 12, float>(LkBatch)","1","1","1","1"\n'
         '"2","lk_stream_kernel<2, 5, 96, 12, float>","18.5","0","90773349","172300"\n')
     rows = bench.parse_ncu_raw_csv(str(csv), "lk_stream_kernel")
     assert len(rows) == 2
