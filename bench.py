@@ -1120,9 +1120,10 @@ def rig_report(dev, pairs, steps: int, warmup: int, oracle_flows=None, half: boo
         for k, (lr, rl) in enumerate(g32):
             olr, orl = oracle_flows[k]
             # how far the method itself lands from the generator's field (FlowRtoL):
-            # with the uncorrected colour gain some pairs' flows wander off
+            # with the uncorrected colour gain some pairs' flows wander off (measured
+            # 0.3 - 2.2 px on five pairs, 10 - 23 px on the other three)
             truth = mean_epe(orl, pairs[k].flow_RtoL)
-            converges[k] = truth <= 1.0
+            converges[k] = truth <= 5.0
             row = {"pair": k, "w": W["widths"][k], "vs_oracle": [mean_epe(lr, olr), mean_epe(rl, orl)],
                    "oracle_RtoL_vs_truth": truth, "converges": converges[k]}
             if sp is not None:

@@ -138,10 +138,16 @@ template <int JW, class Ts>
 __device__ __forceinline__ float sample_target(const TargetBox<Ts>& b, int x, int y, int rx, float2 ref, float2 u) {
     const float2 o = add2(ref, u);
     const float ox = o.x, oy = o.y;
-    const float fx = floorf(ox), fy = floorf(oy);
-    const int ix = (int)fx, iy = (int)fy;
-    const int bcol = rx + (ix - b.fref_x) + kMX;
-    if ((unsigned)bcol < (unsigned)(JW - 1) && (unsigned)(iy - b.fref_y + kMY) <= (unsigned)(2 * kMY)) {
+    // floor(o) through the FP adder: o + 1.5 * 2^23 rounded down holds floor(o)
+    // in its low mantissa bits while |o| < 2^22; larger or non-finite offsets
+    // give integer parts far outside the box and take the global path
+    const float tx = __fadd_rd(ox, 12582912.0f), ty = __fadd_rd(oy, 12582912.0f);
+    const float fx = tx - 12582912.0f, fy = ty - 12582912.0f;
+    const unsigned uix = __float_as_uint(tx) - 0x4B400000u, uiy = __float_as_uint(ty) - 0x4B400000u;
+    const int ix = (int)uix, iy = (int)uiy;
+    const unsigned bcol_u = (unsigned)rx + uix - (unsigned)b.fref_x + (unsigned)kMX;
+    const int bcol = (int)bcol_u;
+    if (bcol_u < (unsigned)(JW - 1) && uiy - (unsigned)(b.fref_y - kMY) <= (unsigned)(2 * kMY)) {
         Taps t;
         t.ax = ox - fx;
         t.ay = oy - fy;
