@@ -173,6 +173,31 @@ def test_each_lk_kernel_matches_oracle(kernel, h, w, iters, radius, start):
     assert np.abs(got - ref).max() <= 1e-3
 
 
+@pytest.mark.parametrize("kernel", [binding.PANO_LK_AUTO, binding.PANO_LK_TILE])
+@pytest.mark.parametrize("h,w,iters,radius,start", [(70, 90, 8, 2, "zero"), (40, 60, 16, 1, "given")])
+def test_lk_kernels_beyond_five_steps_match_oracle(kernel, h, w, iters, radius, start):
+    # more steps than the streamed kernel takes (up to the API's maximum of 16):
+    # AUTO falls back to the tiled kernel
+    T = texture(h, w, 21).astype(np.float32)
+    J = np.roll(T, (0, 1), axis=(0, 1)).astype(np.float32)
+    uin = rng(22).normal(0, 0.5, size=(h, w, 2)).astype(np.float32) if start == "given" else None
+    ref = uin.astype(np.float64) if uin is not None else np.zeros((h, w, 2))
+    for _ in range(iters):
+        ref = oracle.lk_step(T, J, ref, radius, 1e-2)
+    got = host(binding.stage_lk(cuda(T), cuda(J), None if uin is None else cuda(uin), iters=iters, radius=radius,
+                                lam=1e-2, kernel=kernel))
+    assert np.isfinite(got).all()
+    assert epe(got, ref).mean() <= 1e-5
+    assert np.abs(got - ref).max() <= 1e-3
+
+
+def test_streamed_kernel_refuses_more_than_five_steps():
+    T = texture(64, 64, 23).astype(np.float32)
+    with pytest.raises(binding.PanoError) as ei:
+        binding.stage_lk(cuda(T), cuda(T), None, iters=6, kernel=binding.PANO_LK_STREAM)
+    assert ei.value.status == binding.PANO_ERR_UNSUPPORTED
+
+
 def test_upsample_stage_matches_oracle():
     hc, wc, h, w = 23, 37, 45, 73
     uc = rng(8).normal(0, 2, size=(hc, wc, 2)).astype(np.float32)
@@ -276,7 +301,7 @@ def test_end_to_end_small_gray_pair():
 
 
 @pytest.mark.parametrize("h,w,c,levels", [(1, 1, 1, 1), (2, 3, 3, 3), (5, 7, 1, 4), (33, 65, 3, 3),
-                                          (70, 45, 1, 5), (16, 300, 3, 2)])
+                                          (70, 45, 1, 5), (16, 300, 3, 2), (100, 150, 3, 12)])
 def test_end_to_end_edge_sizes(h, w, c, levels):
     g = rng(13)
     base = texture(h + 8, w + 8, 14)
