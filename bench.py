@@ -60,6 +60,8 @@ COUNTER_FILES = {  # (kernel, workload) -> file under profiles/
 }
 # One warp instruction per scheduler per cycle, four schedulers per SM.
 SCHEDULERS_PER_SM = 4
+
+
 # ---------------------------------------------------------------------------
 # host-side helpers (no GPU needed; covered by the CPU tests)
 # ---------------------------------------------------------------------------
@@ -1349,7 +1351,7 @@ def main(argv=None):
                     help="pair: leave out the rig and the 16-bit forms that the default line carries")
     ap.add_argument("--ingest-ncu", metavar="CSV",
                     help="write the profiles/ counters of --counters-kernel from an `ncu -i REPORT --page raw "
-                         "--csv` export (no GPU needed) and exit")
+                         "--csv --print-units base` export (no GPU needed) and exit")
     ap.add_argument("--counters-kernel", default="lk_stream_kernel")
     ap.add_argument("--counters-workload", default=WORKLOAD["workload"])
     ap.add_argument("--counters-command", default="", help="the capture command, recorded with the counters")
