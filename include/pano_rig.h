@@ -63,7 +63,7 @@ typedef struct pano_rig_desc {
 
 typedef struct pano_rig_tuning {
     int kernel;          /* a PANO_LK_* value (pano_flow.h) */
-    int seg_rows;        /* streamed kernel: rows per segment, 0 = automatic (about 192,
+    int seg_rows;        /* streamed kernel: rows per segment, 0 = automatic (about 256,
                             rounded to whole waves of the GPU) */
     int tile_w, tile_h;  /* tiled kernel: output tile; both 0 = the default tile */
     float ms;            /* device time of the level measured by pano_rig_autotune, else 0 */
