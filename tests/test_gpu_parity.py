@@ -374,3 +374,36 @@ def test_full_size_rgb_pair_matches_oracle():
     Fo = oracle.quantize_u8(oracle.blend(pair.L, pair.R, olr, orl, oracle.Params(levels=6)))
     d = np.abs(F.astype(int) - Fo.astype(int))
     assert d.mean() <= 0.05 and d.max() <= 1
+
+
+@pytest.mark.slow
+def test_large_strip_properties():
+    """An 8000 x 12000 RGB u8 pair (288 MB per strip, 32-bit offsets near a
+    quarter of their range), too large for the oracle: properties that hold
+    at any size. Identical strips give zero flow exactly and F = L; an
+    integer translation is recovered in the interior; swapping the strips
+    swaps the flows bit for bit."""
+    h, w = 8000, 12000
+    gen = torch.Generator(device=DEV).manual_seed(5)
+    noise = torch.rand((3, 1, h + 16, w + 16), generator=gen, device=DEV)
+    k = torch.ones((1, 1, 5, 5), device=DEV) / 25.0
+    tex = torch.nn.functional.conv2d(noise, k)                    # (3, 1, h + 12, w + 12), smooth
+    tex = (tex - tex.amin()) / (tex.amax() - tex.amin())
+    img = (tex[:, 0] * 255).round().to(torch.uint8).permute(1, 2, 0).contiguous()   # (h + 12, w + 12, 3)
+    L = img[6:6 + h, 6:6 + w].contiguous()
+    R = img[4:4 + h, 9:9 + w].contiguous()                       # R(p) = L(p + (3, -2))
+    with _ctx(6, h, w, 3) as ctx:
+        z1, z2, F = ctx.stitch_pair(L, L)
+        torch.cuda.synchronize()
+        assert torch.count_nonzero(z1) == 0 and torch.count_nonzero(z2) == 0
+        assert torch.equal(F, L)
+        del z1, z2, F
+        lr, rl = ctx.flow_pair(L, R)
+        rl2, lr2 = ctx.flow_pair(R, L)
+        torch.cuda.synchronize()
+        assert torch.equal(lr, lr2) and torch.equal(rl, rl2)
+        m = 64
+        mean_rl = rl[m:-m, m:-m].reshape(-1, 2).mean(0).cpu().numpy()
+        mean_lr = lr[m:-m, m:-m].reshape(-1, 2).mean(0).cpu().numpy()
+        np.testing.assert_allclose(mean_rl, [3.0, -2.0], atol=0.1)     # FlowRtoL: R(p) = L(p + (3, -2))
+        np.testing.assert_allclose(mean_lr, [-3.0, 2.0], atol=0.1)
