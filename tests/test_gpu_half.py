@@ -117,3 +117,30 @@ def test_half_differs_from_float_only_by_storage_rounding():
         half = gpu_stitch(pair, 4, dt)
         assert 0 < epe(half[0], f32[0]).mean() <= bound
         assert 0 < epe(half[1], f32[1]).mean() <= bound
+
+
+@pytest.mark.slow
+def test_half_rig_full_size_matches_storage_matched_oracle():
+    """The 8-pair, 4000-row rig with 16-bit pyramids (the bench's half-precision
+    rig) against the oracle with the same storage rounding, pair by pair. On
+    the pairs whose flows follow the scene (the exact oracle's FlowRtoL within
+    5 px of the generator's field) the mean EPE stays below 1e-3 px. On the
+    pairs where the uncorrected colour gain sends the iteration off (10-23 px
+    from the field), rare one-ulp differences between the GPU's and the
+    oracle's stored levels are amplified; those stay below 1e-2 px."""
+    widths = (800, 950, 1100, 1250, 1400, 1600, 1800, 2000)
+    pairs = synth.rig_pairs(widths=widths, workers=8)
+    levels = 6
+    exact = [oracle.flow_pair(p.L, p.R, oracle.Params(levels=levels)) for p in pairs]
+    follows = [epe(exact[k][1], p.flow_RtoL).mean() <= 5.0 for k, p in enumerate(pairs)]
+    assert sum(follows) >= 4
+    for dt, fmt in FORMATS:
+        prm = binding.Params(levels=levels, pyr_dtype=dt)
+        with binding.Rig(prm, 4000, widths, canvas_hw=(4000, 9000), canvas_x0=[1125 * k for k in range(8)]) as rig:
+            rig.run([cuda(p.L) for p in pairs], [cuda(p.R) for p in pairs], use_graph=True)
+            torch.cuda.synchronize()
+            got = [tuple(t.cpu().numpy() for t in rig.flows(k)) for k in range(len(pairs))]
+        for k, p in enumerate(pairs):
+            slr, srl = oracle.flow_pair(p.L, p.R, oracle.Params(levels=levels, pyr_fmt=fmt))
+            worst = max(epe(got[k][0], slr).mean(), epe(got[k][1], srl).mean())
+            assert worst <= (1e-3 if follows[k] else 1e-2), (dt, k, worst)
